@@ -1,0 +1,303 @@
+"""Benchmark of the fused reactive-mixture lattice Boltzmann step on GB300.
+
+Workload: the 3D expanding-flame configuration, a periodic 256^3 D3Q27
+lattice with the nine-species, 21-reaction seeded mechanism, T = 300 K and
+a 2000 K spherical kernel of radius 20 (seeded composition noise), mixed
+precision (float populations; double temperature iteration, Stefan-Maxwell
+solve and chemistry).  The same lattice is also stepped with the double
+path for the mixed/double ratio.  One "step" is one full time step of every
+node (ghost/moment/gradient/collision kernels).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead (a bounded sample of the same physics on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MLUPS (M+2 pop sets + chemistry), mixed vs FP64 step, % of HBM roofline"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_oracle_sample(min_seconds: float = 10.0, max_steps: int = 400, warmup: int = 1):
+    """The FP64 oracle on the 32^3 instance of the same physics (radius-8
+    kernel), timed on all host cores."""
+    import oracle
+    import workload as w
+    prob = w.sphere3d_problem(n=32, radius=8.0)
+    o = oracle.Oracle.from_problem(prob)
+    o.step(warmup)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps and (time.perf_counter() - t0) < min_seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 32 ** 3 * n / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"sphere3d 32^3 (radius 8), 9 species / 21 reactions, FP64, {n} steps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import workload as w
+    prob = w.sphere3d_problem(n=32, radius=8.0)
+    o = oracle.Oracle.from_problem(prob)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = 32 ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "sphere3d_32^3_M9_fp64 (bounded sample of sphere3d_256^3_M9)",
+                       "nodes": 32 ** 3, "species": 9, "reactions": 21},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"sphere3d 32^3 (radius 8), FP64, {args.steps} steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import workload as w
+    from paper_2101_01702_gb300 import build
+    build.build()
+    from paper_2101_01702_gb300 import lbm
+
+    n = args.size
+    prob = w.sphere3d_problem(n=n, radius=20.0 * n / 256.0)
+    N = prob.lattice.n_nodes
+    M = prob.species.M
+    S = M + 1
+    precision = lbm.LBM_MIXED if args.precision == "mixed" else lbm.LBM_FP64
+    store = 4 if precision == lbm.LBM_MIXED else 8
+    stream = torch.cuda.Stream()
+
+    def timed_steps(solver, K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        solver.step_async(K)
+        e1.record(stream)
+        st = solver.sync()
+        torch.cuda.synchronize()
+        barrier()
+        if st != lbm.LBM_OK:
+            raise lbm.LBMError(st, "timed steps")
+        return e0.elapsed_time(e1)
+
+    # ---- device-resident run (value) ------------------------------------
+    s = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
+    s.step(args.warmup)
+    with ClockSampler(local) as clk:
+        ms = timed_steps(s, args.steps)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+
+    # ---- per-kernel device times (CUDA events between the launches) -----
+    phases = s.step_timed(args.steps) / args.steps       # ms per launch: ghost, pre, grad, step
+    peak, peak_kind = _peaks()
+    alg_bytes_node = 2 * S * 27 * store                  # one read + one write of every stored population
+    t_step = phases[3] * 1e-3
+    achieved = alg_bytes_node * N / t_step / 1e9
+    step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    e2e = None
+    if not args.skip_e2e:
+        Xh = torch.from_numpy(prob.init.X).pin_memory()
+        Th = torch.from_numpy(prob.init.T).pin_memory()
+        mask = lbm.LBM_F_T | lbm.LBM_F_Y
+        out = torch.empty(lbm.lbm_moments_count(s.ctx, mask), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        st = lbm.lbm_init(s.ctx, Xh.data_ptr(), Th.data_ptr(), None, prob.init.P)
+        st = st or lbm.lbm_step(s.ctx, args.steps)
+        st = st or lbm.lbm_moments(s.ctx, mask, out.data_ptr())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        barrier()
+        if st != lbm.LBM_OK:
+            raise lbm.LBMError(st, "e2e")
+        h2d = (M + 1) * N * 8
+        d2h = out.numel() * 8
+        e2e = {"value": N * args.steps * world / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "note": "lbm_init from pinned host fields + steps + lbm_moments(T, Y) to pinned host"}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+
+    # ---- the double-precision step on the same lattice -------------------
+    fp64 = None
+    if not args.skip_fp64 and precision == lbm.LBM_MIXED:
+        s64 = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64, stream=stream)
+        s64.step(max(1, args.warmup // 2))
+        k64 = max(2, args.steps // 2)
+        ms64 = timed_steps(s64, k64)
+        fp64 = {"mlups": N * k64 * world / (ms64 * 1e-3) / 1e6, "steps": k64,
+                "hbm_frac": 2 * S * 27 * 8 * N / (ms64 * 1e-3 / k64) / 1e9 / peak}
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        cpu = _cpu_oracle_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if precision == lbm.LBM_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"sphere3d_{n}^3_M9_{args.precision}", "nodes": N, "species": M,
+                       "reactions": prob.mech.R, "stored_sets": S, "precision": args.precision,
+                       "parallelism": f"replicas{world}" if world > 1 else "single_gpu",
+                       "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * S * 27 * store * N / 1e9)},
+            "hbm_frac_step": step_frac,
+            "phase_ms": {"ghost": phases[0], "moments": phases[1], "gradients": phases[2],
+                         "collision": phases[3]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_step",
+                         "peak_source": peak_kind,
+                         "algorithmic_bytes_per_node": alg_bytes_node},
+            "fp64_step": fp64,
+            "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * 3,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

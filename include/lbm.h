@@ -1,0 +1,198 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) reactive-mixture lattice Boltzmann
+ * library.
+ *
+ * The library advances the fully kinetic reactive-mixture lattice Boltzmann
+ * model of Sawant, Dorschner and Karlin, "Reactive mixtures with the lattice
+ * Boltzmann model" (arXiv 2101.01702), on a D3Q27 lattice: M species
+ * population sets of which the last is slaved to the mixture (Eq. (strongest),
+ * so M-1 species sets are stored), the mixture mass/momentum set f (Eq. (f))
+ * and the total-energy set g (Eq. (g)).  One time step is pull streaming,
+ * moments, temperature from energy (Eq. (temperature)), the per-node
+ * Stefan-Maxwell system (Eq. (transform1)), the reaction source
+ * (Eqs. (sumfDotc), (fsource)), and the collisions of
+ * Eqs. (finalNumericalEquations), (f) and (g).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status (LBM_OK or a negative LBM_ERR_*); no
+ *     call aborts, traps or prints.  lbm_strerror() names a status.
+ *   - Lattice units: grid spacing and time step are 1.  Node index
+ *     n = x + nx * (y + ny * z); directions i = (cx+1) + 3 (cy+1) + 9 (cz+1)
+ *     with c in {-1,0,1}^3.  Set order: species 0..M-2, then f, then g.
+ *   - Device buffers are owned by the caller (for example torch tensors) and
+ *     are never freed by the library.  Host arrays passed to lbm_create are
+ *     copied; the library keeps no pointer to them.
+ *   - All GPU work is ordered on the CUDA stream given to lbm_create.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,          /* NULL pointer, bad size, unsupported value        */
+    LBM_ERR_CUDA = -2,         /* a CUDA runtime call failed                       */
+    LBM_ERR_NEWTON = -3,       /* temperature iteration did not converge (50 its)  */
+    LBM_ERR_NONFINITE = -4,    /* a density, energy or population became NaN/Inf   */
+    LBM_ERR_NEGATIVE = -5,     /* a species density became negative                */
+    LBM_ERR_PIVOT = -6,        /* zero pivot in the Stefan-Maxwell elimination     */
+    LBM_ERR_UNSUPPORTED = -8   /* valid request this build does not provide        */
+};
+
+enum { LBM_BC_PERIODIC = 0, LBM_BC_EQ_ZEROGRAD_U0LEFT = 1 };
+enum { LBM_FP64 = 0, LBM_MIXED = 1 };
+enum { LBM_THERMO_CONST_CP = 0, LBM_THERMO_POLY7 = 1 };
+enum { LBM_VISC_KINEMATIC = 0, LBM_VISC_RELAXATION = 1 };
+enum { LBM_RXN_ELEMENTARY = 0, LBM_RXN_THIRD_BODY = 1, LBM_RXN_FALLOFF = 2 };
+
+/* Lattice.  y and z are periodic.  bc_x = LBM_BC_PERIODIC wraps x;
+ * LBM_BC_EQ_ZEROGRAD_U0LEFT places ghost nodes beyond both x faces holding
+ * the equilibria of every set at the post-collision moments of the adjacent
+ * boundary node, with zero velocity on the left (paper Sec. 5a, the 1D
+ * flame setup); macroscopic fields used by the gradient stencils continue
+ * with zero gradient.  precision = LBM_FP64 stores and collides in double;
+ * LBM_MIXED stores populations as float deviations from per-set rest
+ * states and collides in float, keeping double for the moments, the
+ * temperature iteration, the Stefan-Maxwell solve and the chemistry. */
+typedef struct {
+    int nx, ny, nz;
+    int bc_x;
+    int precision;
+} lbm_lattice;
+
+/* Species, thermodynamics and transport (paper Secs. 2-3).
+ *   M            number of species, 2 <= M <= 12; species M-1 is slaved.
+ *   W[M]         molar masses; R_a = r_lat / W[a] (paper Sec. 2, after Eq. (eosIdealGas)).
+ *   thermo       LBM_THERMO_CONST_CP: U_a(T) = h_form[a] - R_a T0 + (cp_R[a]-1) R_a (T-T0)
+ *                (Eq. (specHa) with constant heat capacity; h_form is the
+ *                mass-specific formation enthalpy at T0).
+ *                LBM_THERMO_POLY7: single-range 7-coefficient polynomials
+ *                poly7[M][7]: cp/R = a1 + a2 T + ... + a5 T^4,
+ *                h/(R T) = a1 + a2 T/2 + a3 T^2/3 + a4 T^3/4 + a5 T^4/5 + a6/T,
+ *                s/R = a1 ln T + a2 T + a3 T^2/2 + a4 T^3/3 + a5 T^4/4 + a7.
+ *   D[M][M]      binary diffusivities D_ab (Eq. (tauab)), symmetric.
+ *   nu, visc_model   LBM_VISC_KINEMATIC: kinematic viscosity nu, so
+ *                1/omega - 1/2 = nu / (R T) (Eq. (mu) with mu = rho nu);
+ *                LBM_VISC_RELAXATION: 1/omega - 1/2 = nu (mu = nu P).
+ *   Pr           Prandtl number: 1/omega_1 - 1/2 = (1/omega - 1/2) / Pr (Eq. (lambda)).
+ *   r_lat        universal gas constant in lattice units.
+ * Unused arrays (cp_R/h_form for POLY7, poly7 for CONST_CP) may be NULL. */
+typedef struct {
+    int M;
+    const double *W;
+    int thermo;
+    const double *cp_R;
+    const double *h_form;
+    double T0;
+    const double *poly7;
+    const double *D;
+    double nu, Pr, r_lat;
+    int visc_model;
+} lbm_species;
+
+/* Reaction mechanism giving the production rates rho_dot_a of Eq. (sumRhoDot)
+ * (the paper obtains them from Cantera, Sec. 4).  R <= 32 reactions, each
+ * with at most 3 reactant and 3 product molecules.
+ *   nu_f[R][M], nu_r[R][M]   reactant / product stoichiometric coefficients
+ *   k = exp(log_A + b ln(T/T_ref) - theta/T), concentrations c_a = rho_a/W_a
+ *   rtype: ELEMENTARY, THIRD_BODY (rate of progress times [M] = sum eff[k][a] c_a),
+ *          FALLOFF (Lindemann: k = k_inf P_r/(1+P_r), P_r = k0 [M]/k_inf,
+ *          k0 from low[k] = {log_A0, b0, theta0})
+ *   reversible[k] != 0: reverse rate k / K_c with
+ *          K_c = exp(-sum_a dnu_a g_a/(R_U T)) (P0/(r_lat T))^(sum_a dnu_a).
+ * eff and low may be NULL when no reaction needs them. */
+typedef struct {
+    int R;
+    const int *nu_f, *nu_r;
+    const double *log_A, *b, *theta;
+    const int *rtype;
+    const double *eff;
+    const double *low;
+    const int *reversible;
+    double T_ref, P0;
+} lbm_mechanism;
+
+/* Caller-owned device memory, sized by lbm_buffer_sizes():
+ *   pop_a, pop_b  two population buffers, layout [M+1 sets][27][N], double
+ *                 (LBM_FP64) or float deviations (LBM_MIXED); they swap roles
+ *                 every step.  Must be distinct and 16-byte aligned.
+ *   macro         per-node fields, double [(M+8)][N]: T, 1/omega - 1/2,
+ *                 Phi (3), G (3), Y (M).
+ *   ghost         x-face ghost populations [2][M+1][27][ny*nz] in the
+ *                 storage type; may be NULL for periodic x. */
+typedef struct {
+    void *pop_a, *pop_b, *macro, *ghost;
+    size_t pop_bytes, macro_bytes, ghost_bytes;
+} lbm_buffers;
+
+/* Bytes each buffer needs for the lattice and species count. */
+int lbm_buffer_sizes(const lbm_lattice *lat, const lbm_species *sp,
+                     size_t *pop_bytes, size_t *macro_bytes, size_t *ghost_bytes);
+
+/* Validates the description, copies the tables to the device, binds the
+ * buffers and the stream (a cudaStream_t, or NULL for the default stream).
+ * Allocates host state and a 4-byte device status word. */
+int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
+               const lbm_buffers *bufs, void *cuda_stream, lbm_ctx **out);
+
+/* Sets every set to its equilibrium (Eqs. (feq), (feqmix), (gieq)) for mole
+ * fractions X[M][N], temperature T[N], velocity u[3][N] (NULL: at rest) and
+ * a uniform pressure P, with rho = P / (R T) (Eq. (eosIdealGas)).  Pointers
+ * may be host or device memory; host data is staged through pop_b. */
+int lbm_init(lbm_ctx *ctx, const double *X, const double *T, const double *u, double P);
+
+/* Enqueues n time steps on the stream, then waits for them and returns the
+ * first error the kernels recorded (LBM_ERR_NEWTON ... LBM_ERR_PIVOT). */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Enqueues n time steps without waiting; errors surface at lbm_sync(). */
+int lbm_step_async(lbm_ctx *ctx, int n);
+
+/* lbm_step_async with CUDA events recorded on the stream between the
+ * kernels of each step; after waiting, phase_ms[0..3] hold the summed
+ * device time of the ghost-node, moment, gradient and collision kernels
+ * over the n steps.  Returns like lbm_step. */
+int lbm_step_timed(lbm_ctx *ctx, int n, double *phase_ms);
+
+/* Waits for the stream and returns (then clears) the recorded error. */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Macroscopic fields of the current time level (the moments the next
+ * collision sees), double, written to out (host or device) as consecutive
+ * [N] rows in this order for the bits set in mask:
+ *   LBM_F_RHO_A  rho_a, M rows        LBM_F_RHOU  rho u, 3 rows
+ *   LBM_F_RHOE   rho E, 1 row         LBM_F_T     T, 1 row
+ *   LBM_F_P      P = rho R T, 1 row   LBM_F_Y     Y_a, M rows
+ *   LBM_F_J_A    species momenta rho_a u_a, 3M rows (a-major)
+ * Waits for the stream before returning. */
+enum { LBM_F_RHO_A = 1, LBM_F_RHOU = 2, LBM_F_RHOE = 4, LBM_F_T = 8, LBM_F_P = 16,
+       LBM_F_Y = 32, LBM_F_J_A = 64 };
+int lbm_moments(lbm_ctx *ctx, unsigned mask, double *out);
+
+/* Number of doubles lbm_moments writes for mask. */
+size_t lbm_moments_count(const lbm_ctx *ctx, unsigned mask);
+
+/* Current post-collision populations as absolute doubles, layout
+ * [M+1][27][N], copied to host memory out.  Diagnostic accessor. */
+int lbm_get_populations(lbm_ctx *ctx, double *host_out);
+
+/* Device pointer of the buffer that holds the current state (pop_a or
+ * pop_b); with the T row of macro it is everything a checkpoint needs. */
+void *lbm_state_buffer(lbm_ctx *ctx);
+
+/* Frees host state and the status word; never the caller's buffers. */
+int lbm_destroy(lbm_ctx *ctx);
+
+const char *lbm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,506 @@
+// C ABI of the reactive-mixture lattice Boltzmann library (include/lbm.h).
+//
+// Host side only: argument validation, packing of the species and mechanism
+// tables into the constant-memory record the kernels read, buffer binding,
+// the A/B swap of the population buffers, and status reporting.  Every step
+// of the numerical method runs in the kernels of k_fp64.cu / k_mixed.cu.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+struct lbm_ctx {
+    lbm_lattice lat;
+    int M, S, N, slot;
+    cudaStream_t stream;
+    void *buf[2];
+    int cur;                 // index of the buffer holding the current state
+    double *macro;
+    void *ghost;
+    size_t pop_bytes;
+    unsigned *status;        // device status word
+    MechConst mc;            // host copy of the constant-memory record
+};
+
+namespace {
+
+std::mutex g_slot_mutex;
+bool g_slot_used[LBMK_SLOTS] = {false, false, false, false};
+
+bool supported_M(int M) { return M == 2 || M == 3 || M == 9; }
+
+size_t store_size(int precision) { return precision == LBM_MIXED ? sizeof(float) : sizeof(double); }
+
+int map_status(unsigned bits)
+{
+    if (bits & LBMK_BIT_NONFINITE) return LBM_ERR_NONFINITE;
+    if (bits & LBMK_BIT_NEWTON) return LBM_ERR_NEWTON;
+    if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
+    if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
+    return LBM_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+StepArgs args_of(const lbm_ctx *c)
+{
+    StepArgs a;
+    a.slot = c->slot;
+    a.M = c->M;
+    a.nx = c->lat.nx;
+    a.ny = c->lat.ny;
+    a.nz = c->lat.nz;
+    a.N = c->N;
+    a.bc_x = c->lat.bc_x;
+    a.src = c->buf[c->cur];
+    a.dst = c->buf[1 - c->cur];
+    a.macro = c->macro;
+    a.ghost = c->ghost;
+    a.status = c->status;
+    a.stream = c->stream;
+    return a;
+}
+
+// Host evaluation of the thermodynamic functions, used only to choose the
+// rest states that mixed-precision storage subtracts.
+double host_U(const MechConst &mc, int a, double T)
+{
+    if (mc.thermo == 0) return mc.U0[a] + mc.cv[a] * (T - mc.T0);
+    const double *p = mc.poly[a];
+    const double h = p[0] * T + p[1] * T * T / 2 + p[2] * T * T * T / 3 + p[3] * T * T * T * T / 4 +
+                     p[4] * T * T * T * T * T / 5 + p[5];
+    return mc.Ra[a] * (h - T);
+}
+
+double psi_host(int c, double zeta) { return c == 0 ? 1.0 - zeta : 0.5 * zeta; }
+
+// Rest states of every set at the mean initial density and temperature.
+void choose_references(MechConst &mc, int M, const double *X, const double *T, double P, size_t N)
+{
+    double rho_m[LBMK_MAXM] = {0}, T_m = 0.0, rho_t = 0.0;
+    for (size_t n = 0; n < N; ++n) {
+        double m = 0.0;
+        for (int a = 0; a < M; ++a) m += X[(size_t)a * N + n] * mc.W[a];
+        const double rho = P * m / (mc.r_lat * T[n]);
+        for (int a = 0; a < M; ++a) rho_m[a] += rho * X[(size_t)a * N + n] * mc.W[a] / m;
+        T_m += T[n];
+        rho_t += rho;
+    }
+    for (int a = 0; a < M; ++a) rho_m[a] /= (double)N;
+    T_m /= (double)N;
+    rho_t /= (double)N;
+    double inv_m = 0.0, Umix = 0.0;
+    for (int a = 0; a < M; ++a) {
+        inv_m += rho_m[a] / rho_t / mc.W[a];
+        Umix += rho_m[a] / rho_t * host_U(mc, a, T_m);
+    }
+    const double Rm = mc.r_lat * inv_m;
+    const double Hmix = Umix + Rm * T_m;
+    const double rhoE = rho_t * Umix, Pr = rho_t * Rm * T_m;
+    for (int s = 0; s <= M; ++s) {
+        double m0 = 0.0, m2 = 0.0;
+        for (int i = 0; i < LBMK_Q; ++i) {
+            const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+            double v;
+            if (s < M) {
+                const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T_m;
+                const double r = s < M - 1 ? rho_m[s] : rho_t;
+                v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
+            } else {
+                const double w = (cx ? 1.0 / 6.0 : 2.0 / 3.0) * (cy ? 1.0 / 6.0 : 2.0 / 3.0) * (cz ? 1.0 / 6.0 : 2.0 / 3.0);
+                const int c2 = cx * cx + cy * cy + cz * cz;
+                v = w * (rhoE + 4.5 * (Hmix * Pr - rhoE / 3.0) * (c2 - 1.0));
+            }
+            mc.ref[s][i] = (float)v;
+            m0 += (double)mc.ref[s][i];
+            m2 += (double)mc.ref[s][i] * (double)(cx * cx);
+        }
+        mc.ref_m0[s] = m0;
+        mc.ref_m2[s] = m2;
+    }
+}
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int lbm_buffer_sizes(const lbm_lattice *lat, const lbm_species *sp, size_t *pop_bytes, size_t *macro_bytes,
+                     size_t *ghost_bytes)
+{
+    if (!lat || !sp || lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || sp->M < 2 || sp->M > LBMK_MAXM)
+        return LBM_ERR_ARG;
+    if (lat->precision != LBM_FP64 && lat->precision != LBM_MIXED) return LBM_ERR_ARG;
+    const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
+    const size_t S = (size_t)sp->M + 1;
+    const size_t st = store_size(lat->precision);
+    if (pop_bytes) *pop_bytes = S * LBMK_Q * N * st;
+    if (macro_bytes) *macro_bytes = (size_t)(sp->M + MAC_Y) * N * sizeof(double);
+    if (ghost_bytes) *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : 2 * S * LBMK_Q * (size_t)lat->ny * lat->nz * st;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech, const lbm_buffers *bufs,
+               void *cuda_stream, lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!lat || !sp || !mech || !bufs) return LBM_ERR_ARG;
+    if (lat->bc_x != LBM_BC_PERIODIC && lat->bc_x != LBM_BC_EQ_ZEROGRAD_U0LEFT) return LBM_ERR_ARG;
+    size_t need_pop, need_mac, need_gh;
+    int r = lbm_buffer_sizes(lat, sp, &need_pop, &need_mac, &need_gh);
+    if (r != LBM_OK) return r;
+    const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
+    if (N > (size_t)0x7fffffff) return LBM_ERR_ARG;
+    const int M = sp->M;
+    if (!supported_M(M)) return LBM_ERR_UNSUPPORTED;
+    if (!sp->W || !sp->D) return LBM_ERR_ARG;
+    if (sp->thermo == LBM_THERMO_CONST_CP && (!sp->cp_R || !sp->h_form)) return LBM_ERR_ARG;
+    if (sp->thermo == LBM_THERMO_POLY7 && !sp->poly7) return LBM_ERR_ARG;
+    if (sp->thermo != LBM_THERMO_CONST_CP && sp->thermo != LBM_THERMO_POLY7) return LBM_ERR_ARG;
+    if (sp->visc_model != LBM_VISC_KINEMATIC && sp->visc_model != LBM_VISC_RELAXATION) return LBM_ERR_ARG;
+    if (!(sp->r_lat > 0) || !(sp->nu > 0) || !(sp->Pr > 0)) return LBM_ERR_ARG;
+    if (mech->R < 0 || mech->R > LBMK_MAXR) return LBM_ERR_ARG;
+    if (mech->R > 0 && (!mech->nu_f || !mech->nu_r || !mech->log_A || !mech->b || !mech->theta || !mech->rtype ||
+                        !mech->reversible))
+        return LBM_ERR_ARG;
+    if (!bufs->pop_a || !bufs->pop_b || bufs->pop_a == bufs->pop_b || !bufs->macro) return LBM_ERR_ARG;
+    if (bufs->pop_bytes < need_pop || bufs->macro_bytes < need_mac) return LBM_ERR_ARG;
+    if (need_gh && (!bufs->ghost || bufs->ghost_bytes < need_gh)) return LBM_ERR_ARG;
+    if (((uintptr_t)bufs->pop_a | (uintptr_t)bufs->pop_b | (uintptr_t)bufs->macro) & 15u) return LBM_ERR_ARG;
+
+    MechConst mc;
+    memset(&mc, 0, sizeof(mc));
+    mc.M = M;
+    mc.R = mech->R;
+    mc.thermo = sp->thermo;
+    mc.visc_model = sp->visc_model;
+    mc.T0 = sp->T0;
+    mc.nu = sp->nu;
+    mc.Pr = sp->Pr;
+    mc.r_lat = sp->r_lat;
+    for (int a = 0; a < M; ++a) {
+        if (!(sp->W[a] > 0)) return LBM_ERR_ARG;
+        mc.W[a] = sp->W[a];
+        mc.invW[a] = 1.0 / sp->W[a];
+        mc.Ra[a] = sp->r_lat / sp->W[a];
+        if (sp->thermo == LBM_THERMO_CONST_CP) {
+            mc.cpR[a] = sp->cp_R[a];
+            mc.cv[a] = (sp->cp_R[a] - 1.0) * mc.Ra[a];
+            mc.U0[a] = sp->h_form[a] - mc.Ra[a] * sp->T0;
+        } else {
+            for (int k = 0; k < 7; ++k) mc.poly[a][k] = sp->poly7[7 * a + k];
+        }
+        for (int b = 0; b < M; ++b) {
+            const double D = sp->D[M * a + b];
+            if (a != b) {
+                if (!(D > 0) || D != sp->D[M * b + a]) return LBM_ERR_ARG;
+                mc.inv_WWD[a][b] = 1.0 / (sp->W[a] * sp->W[b] * D);
+                mc.inv_WWD_f[a][b] = (float)mc.inv_WWD[a][b];
+            }
+        }
+    }
+    if (mech->R > 0 && !(mech->T_ref > 0)) return LBM_ERR_ARG;
+    mc.log_T_ref = mech->R > 0 ? log(mech->T_ref) : 0.0;
+    bool need_P0 = false;
+    for (int k = 0; k < mech->R; ++k) {
+        const int t = mech->rtype[k];
+        if (t < 0 || t > 2) return LBM_ERR_ARG;
+        if (t != 0 && !mech->eff) return LBM_ERR_ARG;
+        if (t == 2 && !mech->low) return LBM_ERR_ARG;
+        mc.rtype[k] = t;
+        mc.rev[k] = mech->reversible[k] ? 1 : 0;
+        need_P0 |= mc.rev[k] != 0;
+        mc.log_A[k] = mech->log_A[k];
+        mc.b[k] = mech->b[k];
+        mc.theta[k] = mech->theta[k];
+        if (t == 2)
+            for (int d = 0; d < 3; ++d) mc.low[k][d] = mech->low[3 * k + d];
+        int nr = 0, np = 0, nd = 0;
+        double dn = 0.0;
+        for (int a = 0; a < M; ++a) {
+            const int f = mech->nu_f[M * k + a], g = mech->nu_r[M * k + a];
+            if (f < 0 || g < 0) return LBM_ERR_ARG;
+            for (int j = 0; j < f; ++j) { if (nr >= 3) return LBM_ERR_ARG; mc.reac[k][nr++] = a; }
+            for (int j = 0; j < g; ++j) { if (np >= 3) return LBM_ERR_ARG; mc.prod[k][np++] = a; }
+            if (g != f) {
+                if (nd >= 6) return LBM_ERR_ARG;
+                mc.dnu_sp[k][nd] = a;
+                mc.dnu_v[k][nd++] = g - f;
+                dn += g - f;
+            }
+            if (t != 0) mc.eff[k][a] = mech->eff[M * k + a];
+        }
+        if (nr == 0) return LBM_ERR_ARG;
+        mc.nreac[k] = nr;
+        mc.nprod[k] = np;
+        mc.ndnu[k] = nd;
+        mc.dn[k] = dn;
+    }
+    if (need_P0) {
+        if (!(mech->P0 > 0)) return LBM_ERR_ARG;
+        mc.log_P0_over_r = log(mech->P0 / sp->r_lat);
+    }
+
+    int slot = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_slot_mutex);
+        for (int s = 0; s < LBMK_SLOTS; ++s)
+            if (!g_slot_used[s]) { slot = s; g_slot_used[s] = true; break; }
+    }
+    if (slot < 0) return LBM_ERR_UNSUPPORTED;
+
+    lbm_ctx *c = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
+    if (!c) {
+        std::lock_guard<std::mutex> lk(g_slot_mutex);
+        g_slot_used[slot] = false;
+        return LBM_ERR_ARG;
+    }
+    c->lat = *lat;
+    c->M = M;
+    c->S = M + 1;
+    c->N = (int)N;
+    c->slot = slot;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->buf[0] = bufs->pop_a;
+    c->buf[1] = bufs->pop_b;
+    c->cur = 0;
+    c->macro = (double *)bufs->macro;
+    c->ghost = bufs->ghost;
+    c->pop_bytes = need_pop;
+    c->mc = mc;
+    int st = check_cuda(cudaMalloc((void **)&c->status, 16));
+    if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
+    if (st == LBM_OK) {
+        const int e = lat->precision == LBM_MIXED ? lbmk::upload_mixed(slot, c->mc, c->stream)
+                                                  : lbmk::upload_fp64(slot, c->mc, c->stream);
+        st = e ? LBM_ERR_CUDA : LBM_OK;
+    }
+    if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
+    if (st != LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, double P)
+{
+    if (!c || !X || !T || !(P > 0)) return LBM_ERR_ARG;
+    const size_t N = (size_t)c->N, M = (size_t)c->M;
+    const bool dX = is_device_ptr(X), dT = is_device_ptr(T), du = u ? is_device_ptr(u) : dX;
+    if (dX != dT || dX != du) return LBM_ERR_ARG;     // all host or all device
+    int st = LBM_OK;
+    if (c->lat.precision == LBM_MIXED) {
+        // rest states from the mean initial state
+        const double *hX = X, *hT = T;
+        double *tmpX = nullptr, *tmpT = nullptr;
+        if (dX) {
+            tmpX = (double *)malloc(M * N * sizeof(double));
+            tmpT = (double *)malloc(N * sizeof(double));
+            if (!tmpX || !tmpT) { free(tmpX); free(tmpT); return LBM_ERR_ARG; }
+            st = check_cuda(cudaMemcpy(tmpX, X, M * N * sizeof(double), cudaMemcpyDeviceToHost));
+            if (st == LBM_OK) st = check_cuda(cudaMemcpy(tmpT, T, N * sizeof(double), cudaMemcpyDeviceToHost));
+            hX = tmpX;
+            hT = tmpT;
+        }
+        if (st == LBM_OK) {
+            choose_references(c->mc, c->M, hX, hT, P, N);
+            st = lbmk::upload_mixed(c->slot, c->mc, c->stream) ? LBM_ERR_CUDA : LBM_OK;
+        }
+        free(tmpX);
+        free(tmpT);
+        if (st != LBM_OK) return st;
+    }
+    const double *dXp = X, *dTp = T, *dup = u;
+    if (!dX) {
+        // stage host fields through the second population buffer
+        double *stage = (double *)c->buf[1 - c->cur];
+        const size_t need = (M + 4) * N * sizeof(double);
+        if (need > c->pop_bytes) return LBM_ERR_ARG;
+        st = check_cuda(cudaMemcpyAsync(stage, X, M * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (st == LBM_OK)
+            st = check_cuda(cudaMemcpyAsync(stage + M * N, T, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (st == LBM_OK && u)
+            st = check_cuda(cudaMemcpyAsync(stage + (M + 1) * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice,
+                                            c->stream));
+        if (st != LBM_OK) return st;
+        dXp = stage;
+        dTp = stage + M * N;
+        dup = u ? stage + (M + 1) * N : nullptr;
+    }
+    StepArgs a = args_of(c);
+    a.dst = c->buf[c->cur];
+    const int e = c->lat.precision == LBM_MIXED ? lbmk::init_mixed(a, dXp, dTp, dup, P)
+                                                : lbmk::init_fp64(a, dXp, dTp, dup, P);
+    if (e) return LBM_ERR_CUDA;
+    st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
+    if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
+    return st;
+}
+
+int lbm_step_async(lbm_ctx *c, int n)
+{
+    if (!c || n < 0) return LBM_ERR_ARG;
+    for (int t = 0; t < n; ++t) {
+        StepArgs a = args_of(c);
+        const int e = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a) : lbmk::step_fp64(a);
+        if (e) return LBM_ERR_CUDA;
+        c->cur = 1 - c->cur;
+    }
+    return LBM_OK;
+}
+
+int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
+{
+    if (!c || n < 0 || !phase_ms) return LBM_ERR_ARG;
+    for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) {
+            for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
+            return LBM_ERR_CUDA;
+        }
+    int st = LBM_OK;
+    for (int t = 0; t < n && st == LBM_OK; ++t) {
+        StepArgs a = args_of(c);
+        const int e = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a, ev) : lbmk::step_fp64(a, ev);
+        if (e) { st = LBM_ERR_CUDA; break; }
+        c->cur = 1 - c->cur;
+        if (cudaEventSynchronize(ev[4]) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
+        for (int k = 0; k < 4; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            phase_ms[k] += ms;
+        }
+    }
+    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    if (st != LBM_OK) return st;
+    return lbm_sync(c);
+}
+
+int lbm_sync(lbm_ctx *c)
+{
+    if (!c) return LBM_ERR_ARG;
+    unsigned bits = 0;
+    int st = check_cuda(cudaMemcpyAsync(&bits, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
+    if (st != LBM_OK) return st;
+    if (bits) {
+        st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
+        if (st != LBM_OK) return st;
+    }
+    return map_status(bits);
+}
+
+int lbm_step(lbm_ctx *c, int n)
+{
+    int st = lbm_step_async(c, n);
+    if (st != LBM_OK) return st;
+    return lbm_sync(c);
+}
+
+size_t lbm_moments_count(const lbm_ctx *c, unsigned mask)
+{
+    if (!c) return 0;
+    size_t rows = 0;
+    if (mask & LBM_F_RHO_A) rows += c->M;
+    if (mask & LBM_F_RHOU) rows += 3;
+    if (mask & LBM_F_RHOE) rows += 1;
+    if (mask & LBM_F_T) rows += 1;
+    if (mask & LBM_F_P) rows += 1;
+    if (mask & LBM_F_Y) rows += c->M;
+    if (mask & LBM_F_J_A) rows += 3 * (size_t)c->M;
+    return rows * (size_t)c->N;
+}
+
+int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
+{
+    if (!c || !out || mask == 0 || (mask & ~127u)) return LBM_ERR_ARG;
+    const size_t count = lbm_moments_count(c, mask);
+    const bool dev = is_device_ptr(out);
+    double *target = out;
+    if (!dev) {
+        if (count * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+        target = (double *)c->buf[1 - c->cur];
+    }
+    StepArgs a = args_of(c);
+    const int e = c->lat.precision == LBM_MIXED ? lbmk::moments_mixed(a, mask, target)
+                                                : lbmk::moments_fp64(a, mask, target);
+    if (e) return LBM_ERR_CUDA;
+    if (!dev) {
+        int st = check_cuda(cudaMemcpyAsync(out, target, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (st != LBM_OK) return st;
+    }
+    return lbm_sync(c);
+}
+
+int lbm_get_populations(lbm_ctx *c, double *host_out)
+{
+    if (!c || !host_out) return LBM_ERR_ARG;
+    const size_t cnt = (size_t)c->S * LBMK_Q * c->N;
+    int st = check_cuda(cudaStreamSynchronize(c->stream));
+    if (st != LBM_OK) return st;
+    if (c->lat.precision == LBM_FP64)
+        return check_cuda(cudaMemcpy(host_out, c->buf[c->cur], cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    float *tmp = (float *)malloc(cnt * sizeof(float));
+    if (!tmp) return LBM_ERR_ARG;
+    st = check_cuda(cudaMemcpy(tmp, c->buf[c->cur], cnt * sizeof(float), cudaMemcpyDeviceToHost));
+    if (st == LBM_OK)
+        for (int s = 0; s < c->S; ++s)
+            for (int i = 0; i < LBMK_Q; ++i) {
+                const size_t base = ((size_t)s * LBMK_Q + i) * c->N;
+                for (int n = 0; n < c->N; ++n) host_out[base + n] = (double)tmp[base + n] + (double)c->mc.ref[s][i];
+            }
+    free(tmp);
+    return st;
+}
+
+void *lbm_state_buffer(lbm_ctx *c) { return c ? c->buf[c->cur] : nullptr; }
+
+int lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (c->status) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->status);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_slot_mutex);
+        if (c->slot >= 0 && c->slot < LBMK_SLOTS) g_slot_used[c->slot] = false;
+    }
+    free(c);
+    return LBM_OK;
+}
+
+const char *lbm_strerror(int s)
+{
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_NEWTON: return "temperature iteration did not converge";
+    case LBM_ERR_NONFINITE: return "non-finite density, energy or population";
+    case LBM_ERR_NEGATIVE: return "negative species density";
+    case LBM_ERR_PIVOT: return "zero pivot in the Stefan-Maxwell solve";
+    case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

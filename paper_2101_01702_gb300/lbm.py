@@ -1,0 +1,294 @@
+"""Thin ctypes binding of liblbm.so (include/lbm.h).
+
+The functions below carry the C names and only marshal arguments; every
+step of the lattice Boltzmann method runs in the library's CUDA kernels.
+PyTorch provides the device buffers and the stream.  Importing this module
+fails with ImportError when the compiled library is absent: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "liblbm.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2101_01702_gb300.build.build()")
+_lib = C.CDLL(str(_LIB_PATH))
+
+LBM_OK = 0
+LBM_ERR_ARG = -1
+LBM_ERR_CUDA = -2
+LBM_ERR_NEWTON = -3
+LBM_ERR_NONFINITE = -4
+LBM_ERR_NEGATIVE = -5
+LBM_ERR_PIVOT = -6
+LBM_ERR_UNSUPPORTED = -8
+LBM_BC_PERIODIC = 0
+LBM_BC_EQ_ZEROGRAD_U0LEFT = 1
+LBM_FP64 = 0
+LBM_MIXED = 1
+LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2, 4, 8, 16, 32, 64
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class lbm_lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc_x", C.c_int), ("precision", C.c_int)]
+
+
+class lbm_species(C.Structure):
+    _fields_ = [("M", C.c_int), ("W", _dp), ("thermo", C.c_int), ("cp_R", _dp), ("h_form", _dp),
+                ("T0", C.c_double), ("poly7", _dp), ("D", _dp), ("nu", C.c_double), ("Pr", C.c_double),
+                ("r_lat", C.c_double), ("visc_model", C.c_int)]
+
+
+class lbm_mechanism(C.Structure):
+    _fields_ = [("R", C.c_int), ("nu_f", _ip), ("nu_r", _ip), ("log_A", _dp), ("b", _dp), ("theta", _dp),
+                ("rtype", _ip), ("eff", _dp), ("low", _dp), ("reversible", _ip), ("T_ref", C.c_double),
+                ("P0", C.c_double)]
+
+
+class lbm_buffers(C.Structure):
+    _fields_ = [("pop_a", C.c_void_p), ("pop_b", C.c_void_p), ("macro", C.c_void_p), ("ghost", C.c_void_p),
+                ("pop_bytes", C.c_size_t), ("macro_bytes", C.c_size_t), ("ghost_bytes", C.c_size_t)]
+
+
+_sz = C.c_size_t
+_lib.lbm_buffer_sizes.argtypes = [C.POINTER(lbm_lattice), C.POINTER(lbm_species), C.POINTER(_sz),
+                                  C.POINTER(_sz), C.POINTER(_sz)]
+_lib.lbm_create.argtypes = [C.POINTER(lbm_lattice), C.POINTER(lbm_species), C.POINTER(lbm_mechanism),
+                            C.POINTER(lbm_buffers), C.c_void_p, C.POINTER(C.c_void_p)]
+_lib.lbm_init.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]
+_lib.lbm_step.argtypes = [C.c_void_p, C.c_int]
+_lib.lbm_step_async.argtypes = [C.c_void_p, C.c_int]
+_lib.lbm_sync.argtypes = [C.c_void_p]
+_lib.lbm_step_timed.argtypes = [C.c_void_p, C.c_int, _dp]
+_lib.lbm_moments.argtypes = [C.c_void_p, C.c_uint, C.c_void_p]
+_lib.lbm_moments_count.argtypes = [C.c_void_p, C.c_uint]
+_lib.lbm_moments_count.restype = C.c_size_t
+_lib.lbm_get_populations.argtypes = [C.c_void_p, _dp]
+_lib.lbm_state_buffer.argtypes = [C.c_void_p]
+_lib.lbm_state_buffer.restype = C.c_void_p
+_lib.lbm_destroy.argtypes = [C.c_void_p]
+_lib.lbm_strerror.argtypes = [C.c_int]
+_lib.lbm_strerror.restype = C.c_char_p
+
+EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_timed", "lbm_sync",
+            "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
+            "lbm_strerror"]
+
+
+def library_path() -> str:
+    return str(_LIB_PATH)
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {lbm_strerror(status)} ({status})" if what else lbm_strerror(status))
+
+
+def _check(st: int, what: str) -> int:
+    if st != LBM_OK:
+        raise LBMError(st, what)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers (argument marshalling only)
+# ---------------------------------------------------------------------------
+def lbm_buffer_sizes(lat: lbm_lattice, sp: lbm_species):
+    a, b, c = _sz(), _sz(), _sz()
+    _check(_lib.lbm_buffer_sizes(C.byref(lat), C.byref(sp), C.byref(a), C.byref(b), C.byref(c)), "lbm_buffer_sizes")
+    return a.value, b.value, c.value
+
+
+def lbm_create(lat, sp, mech, bufs, stream: int):
+    h = C.c_void_p()
+    st = _lib.lbm_create(C.byref(lat), C.byref(sp), C.byref(mech), C.byref(bufs), C.c_void_p(stream), C.byref(h))
+    _check(st, "lbm_create")
+    return h
+
+
+def lbm_init(ctx, X_ptr: int, T_ptr: int, u_ptr, P: float) -> int:
+    return _lib.lbm_init(ctx, C.c_void_p(X_ptr), C.c_void_p(T_ptr), C.c_void_p(u_ptr) if u_ptr else None,
+                         float(P))
+
+
+def lbm_step(ctx, n: int) -> int:
+    return _lib.lbm_step(ctx, int(n))
+
+
+def lbm_step_async(ctx, n: int) -> int:
+    return _lib.lbm_step_async(ctx, int(n))
+
+
+def lbm_step_timed(ctx, n: int, phase_ms: np.ndarray) -> int:
+    assert phase_ms.dtype == np.float64 and phase_ms.size >= 4
+    return _lib.lbm_step_timed(ctx, int(n), phase_ms.ctypes.data_as(_dp))
+
+
+def lbm_sync(ctx) -> int:
+    return _lib.lbm_sync(ctx)
+
+
+def lbm_moments(ctx, mask: int, out_ptr: int) -> int:
+    return _lib.lbm_moments(ctx, C.c_uint(mask), C.c_void_p(out_ptr))
+
+
+def lbm_moments_count(ctx, mask: int) -> int:
+    return _lib.lbm_moments_count(ctx, C.c_uint(mask))
+
+
+def lbm_get_populations(ctx, out: np.ndarray) -> int:
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    return _lib.lbm_get_populations(ctx, out.ctypes.data_as(_dp))
+
+
+def lbm_state_buffer(ctx) -> int:
+    return _lib.lbm_state_buffer(ctx)
+
+
+def lbm_destroy(ctx) -> int:
+    return _lib.lbm_destroy(ctx)
+
+
+def lbm_strerror(st: int) -> str:
+    return _lib.lbm_strerror(int(st)).decode()
+
+
+# ---------------------------------------------------------------------------
+# Convenience: a problem description plus torch-owned device buffers
+# ---------------------------------------------------------------------------
+class Solver:
+    """Owns torch buffers for one lattice and drives the C ABI.
+
+    lattice/species/mech follow workload.problem (numpy arrays).  The
+    tables are passed to lbm_create, which copies them.
+    """
+
+    def __init__(self, lattice, species, mech, precision: int = LBM_FP64, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.M = species.M
+        self.S = self.M + 1
+        self.N = lattice.nx * lattice.ny * lattice.nz
+        self.precision = precision
+        self._keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        def i(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            self._keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision)
+        self.sp = lbm_species(self.M, d(species.W), species.thermo, d(species.cp_R), d(species.h_form),
+                              species.T0, d(species.poly7), d(species.D), species.nu, species.Pr,
+                              species.r_lat, species.visc_model)
+        R = mech.R
+        self.mech = lbm_mechanism(R, i(mech.nu_f.reshape(R, -1)) if R else None,
+                                  i(mech.nu_r.reshape(R, -1)) if R else None,
+                                  d(mech.log_A) if R else None, d(mech.b) if R else None,
+                                  d(mech.theta) if R else None, i(mech.rtype) if R else None,
+                                  d(mech.eff) if R else None, d(mech.low) if R else None,
+                                  i(mech.reversible) if R else None, mech.T_ref, mech.P0)
+        pop_b, mac_b, gh_b = lbm_buffer_sizes(self.lat, self.sp)
+        with torch.cuda.device(self.device):
+            self.pop = [torch.empty(pop_b, dtype=torch.uint8, device=self.device) for _ in range(2)]
+            self.macro = torch.zeros(mac_b // 8, dtype=torch.float64, device=self.device)
+            self.ghost = torch.empty(max(gh_b, 16), dtype=torch.uint8, device=self.device)
+        self.bufs = lbm_buffers(self.pop[0].data_ptr(), self.pop[1].data_ptr(), self.macro.data_ptr(),
+                                self.ghost.data_ptr() if gh_b else None, pop_b, mac_b, gh_b)
+        self.ctx = lbm_create(self.lat, self.sp, self.mech, self.bufs, self.stream.cuda_stream)
+
+    @classmethod
+    def from_problem(cls, prob, precision: int = LBM_FP64, init: bool = True, **kw):
+        s = cls(prob.lattice, prob.species, prob.mech, precision, **kw)
+        if init:
+            s.init(prob.init.X, prob.init.T, prob.init.u, prob.init.P)
+        return s
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, X, T, u, P):
+        """X[M,N], T[N], u[3,N] or None: numpy (host) or torch (device) arrays."""
+        torch = self.torch
+        if isinstance(X, torch.Tensor):
+            Xt = X.contiguous().to(torch.float64)
+            Tt = T.contiguous().to(torch.float64)
+            ut = None if u is None else u.contiguous().to(torch.float64)
+            keep = (Xt, Tt, ut)
+            st = lbm_init(self.ctx, Xt.data_ptr(), Tt.data_ptr(), ut.data_ptr() if ut is not None else None, P)
+            del keep
+        else:
+            Xh = np.ascontiguousarray(X, dtype=np.float64)
+            Th = np.ascontiguousarray(T, dtype=np.float64)
+            uh = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+            st = lbm_init(self.ctx, Xh.ctypes.data, Th.ctypes.data, uh.ctypes.data if uh is not None else None, P)
+        _check(st, "lbm_init")
+
+    def step(self, n: int = 1, check: bool = True) -> int:
+        st = lbm_step(self.ctx, n)
+        if check:
+            _check(st, "lbm_step")
+        return st
+
+    def step_async(self, n: int = 1):
+        _check(lbm_step_async(self.ctx, n), "lbm_step_async")
+
+    def step_timed(self, n: int = 1):
+        """Runs n steps; returns per-phase device milliseconds summed over
+        them (ghost, moments, gradients, collision)."""
+        ph = np.zeros(4)
+        _check(lbm_step_timed(self.ctx, n, ph), "lbm_step_timed")
+        return ph
+
+    def sync(self) -> int:
+        return lbm_sync(self.ctx)
+
+    def moments(self, mask: int = LBM_F_RHO_A | LBM_F_RHOU | LBM_F_RHOE | LBM_F_T, device: bool = False):
+        """Dictionary of fields (numpy on host, or torch on the device)."""
+        torch = self.torch
+        count = lbm_moments_count(self.ctx, mask)
+        if device:
+            out = torch.empty(count, dtype=torch.float64, device=self.device)
+            _check(lbm_moments(self.ctx, mask, out.data_ptr()), "lbm_moments")
+        else:
+            out = np.empty(count, dtype=np.float64)
+            _check(lbm_moments(self.ctx, mask, out.ctypes.data), "lbm_moments")
+        res, row, N, M = {}, 0, self.N, self.M
+        for bit, name, rows in ((LBM_F_RHO_A, "rho_a", M), (LBM_F_RHOU, "rhou", 3), (LBM_F_RHOE, "rhoE", 1),
+                                (LBM_F_T, "T", 1), (LBM_F_P, "P", 1), (LBM_F_Y, "Y", M), (LBM_F_J_A, "j_a", 3 * M)):
+            if mask & bit:
+                blk = out[row * N:(row + rows) * N]
+                res[name] = blk.reshape(rows, N) if rows > 1 else blk.reshape(N)
+                row += rows
+        if "j_a" in res:
+            res["j_a"] = res["j_a"].reshape(M, 3, N)
+        return res
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((self.S, 27, self.N), dtype=np.float64)
+        _check(lbm_get_populations(self.ctx, out), "lbm_get_populations")
+        return out

@@ -1,0 +1,137 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Error metric per moment field F: max|F_gpu - F_ref| / max|F_ref| (species
+fields one by one).  Bars:
+  * FP64 GPU path: 1e-10 in every moment field (mass fractions, densities,
+    momentum, energy, temperature);
+  * mixed path (float populations, double chemistry/solve/temperature):
+    1e-4 in mass fractions (normalised by each species' maximum) and
+    temperature.
+Sizes span several 128-thread blocks with a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import workload as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2101_01702_gb300 import build
+    build.build()
+    from paper_2101_01702_gb300 import lbm as L
+    return L
+
+
+def _fields(m):
+    out = {}
+    for a in range(m["rho_a"].shape[0]):
+        out[f"rho_a{a}"] = m["rho_a"][a]
+        out[f"Y{a}"] = m["Y"][a]
+    for d in range(3):
+        out[f"rhou{d}"] = m["rhou"][d]
+    out["rhoE"] = m["rhoE"]
+    out["T"] = m["T"]
+    return out
+
+
+def _gpu_moments(s, L):
+    m = s.moments(L.LBM_F_RHO_A | L.LBM_F_RHOU | L.LBM_F_RHOE | L.LBM_F_T | L.LBM_F_Y)
+    return _fields(m)
+
+
+def _oracle_moments(o):
+    return _fields(o.moments())
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _compare(gpu, ref, tol, keys=None):
+    worst = {}
+    for k in (keys or ref):
+        worst[k] = _rel(gpu[k], ref[k])
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    assert not bad, f"fields above {tol}: {bad}"
+    return worst
+
+
+def _run_pair(orc, L, prob, steps, precision):
+    o = orc.Oracle.from_problem(prob)
+    s = L.Solver.from_problem(prob, precision=precision)
+    assert o.step(steps) == 0
+    assert s.step(steps, check=False) == L.LBM_OK
+    return s, o
+
+
+@pytest.mark.parametrize("steps", [1, 200])
+def test_fp64_config1_against_oracle(orc, lbm, steps):
+    prob = w.config1_problem()
+    s, o = _run_pair(orc, lbm, prob, steps, lbm.LBM_FP64)
+    _compare(_gpu_moments(s, lbm), _oracle_moments(o), 1e-10)
+
+
+def test_fp64_populations_small_periodic(orc, lbm):
+    prob = w.small_periodic_problem(n=5, seed=3, M3_rate_A=20.0)
+    s, o = _run_pair(orc, lbm, prob, 30, lbm.LBM_FP64)
+    gp = s.populations()                    # [S][27][N]
+    op = o.get_pop().transpose(1, 2, 0)     # [N][S][27] -> [S][27][N]
+    for k in range(gp.shape[0]):
+        assert _rel(gp[k], op[k]) <= 1e-12, k
+
+
+def test_fp64_ragged_box_binary_and_ghosts(orc, lbm):
+    """Non-periodic x with ghost nodes on a box that is not a multiple of the
+    thread-block size (three-gas physics)."""
+    from workload.problem import LatticeSpec, BC_EQ_ZEROGRAD_U0LEFT
+    base = w.small_periodic_problem(n=3, seed=4, M3_rate_A=20.0)
+    nx, ny, nz = 37, 5, 3
+    N = nx * ny * nz
+    rng = np.random.default_rng(4)
+    X = np.array([[0.3], [0.5], [0.2]]) + rng.uniform(-0.1, 0.1, (3, N))
+    X /= X.sum(axis=0, keepdims=True)
+    T = 1.0 + rng.uniform(0, 0.5, N)
+    u = rng.uniform(-0.01, 0.01, (3, N))
+    base.lattice = LatticeSpec(nx, ny, nz, BC_EQ_ZEROGRAD_U0LEFT)
+    base.init.X, base.init.T, base.init.u = X, T, u
+    s, o = _run_pair(orc, lbm, base, 50, lbm.LBM_FP64)
+    _compare(_gpu_moments(s, lbm), _oracle_moments(o), 1e-10)
+
+
+def test_fp64_flame1d_with_boundaries(orc, lbm):
+    prob = w.flame1d_problem(nx=512)
+    s, o = _run_pair(orc, lbm, prob, 200, lbm.LBM_FP64)
+    _compare(_gpu_moments(s, lbm), _oracle_moments(o), 1e-10)
+
+
+def test_fp64_sphere_nine_species(orc, lbm):
+    prob = w.sphere3d_problem(shape=(25, 23, 21), radius=6.0)
+    s, o = _run_pair(orc, lbm, prob, 40, lbm.LBM_FP64)
+    _compare(_gpu_moments(s, lbm), _oracle_moments(o), 1e-10)
+
+
+def _mixed_errors(gpu, ref, M):
+    err = {"T": _rel(gpu["T"], ref["T"])}
+    for a in range(M):
+        err[f"Y{a}"] = _rel(gpu[f"Y{a}"], ref[f"Y{a}"])
+    return err
+
+
+def test_mixed_sphere_against_oracle(orc, lbm):
+    prob = w.sphere3d_problem(shape=(25, 23, 21), radius=6.0)
+    s, o = _run_pair(orc, lbm, prob, 100, lbm.LBM_MIXED)
+    err = _mixed_errors(_gpu_moments(s, lbm), _oracle_moments(o), 9)
+    assert max(err.values()) <= 1e-4, err
+
+
+def test_mixed_config1_against_oracle(orc, lbm):
+    prob = w.config1_problem()
+    s, o = _run_pair(orc, lbm, prob, 200, lbm.LBM_MIXED)
+    err = _mixed_errors(_gpu_moments(s, lbm), _oracle_moments(o), 3)
+    assert max(err.values()) <= 1e-4, err

@@ -313,21 +313,23 @@ def flame1d_problem(nx: int = 4096, ny: int = 4, nz: int = 4, phi: float = 1.0,
 
 def sphere3d_problem(n: int = 256, radius: float = 20.0, T_u: float = MECH9_T_UNBURNT,
                      T_hot: float = 2000.0, seed: int = 1703,
-                     chem_scale: float = MECH9_CHEM_SCALE) -> Problem:
-    """Periodic n^3 cube, phi = 1 mixture with seeded composition noise, hot
-    sphere |x - c| < radius (c = n/2 on every axis) at T_hot, at rest."""
+                     chem_scale: float = MECH9_CHEM_SCALE, shape=None) -> Problem:
+    """Periodic box (n^3, or shape = (nx, ny, nz)), phi = 1 mixture with seeded
+    composition noise, hot sphere |x - c| < radius (c = box centre, integer
+    division) at T_hot, at rest."""
     sp, mech = mech9(chem_scale)
-    N = n ** 3
+    nx, ny, nz = (n, n, n) if shape is None else shape
+    N = nx * ny * nz
     X = _normalise_with_noise(PHI1_X, N, seed)
     idx = np.arange(N)
-    x = idx % n
-    y = (idx // n) % n
-    z = idx // (n * n)
-    c = n // 2
-    r2 = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    r2 = (x - nx // 2) ** 2 + (y - ny // 2) ** 2 + (z - nz // 2) ** 2
     T = np.full(N, T_u)
     T[r2 < radius * radius] = T_hot
-    return Problem(f"sphere3d_{n}^3_M9", LatticeSpec(n, n, n, BC_PERIODIC), sp, mech,
+    name = f"sphere3d_{n}^3_M9" if shape is None else f"sphere3d_{nx}x{ny}x{nz}_M9"
+    return Problem(name, LatticeSpec(nx, ny, nz, BC_PERIODIC), sp, mech,
                    InitFields(X=X, T=T, u=None, P=mech.P0), steps=1000)
 
 
