@@ -585,7 +585,7 @@ static int moments_node(orc_state *s, size_t n)
         double Ya = s->rho_a[n * M + a] / rho;
         s->Y[n * M + a] = Ya;
         inv_m += Ya / s->W[a];
-        if (s->rho_a[n * M + a] < 0.0 && st == ORC_OK) st = ORC_ERR_NEGATIVE;
+        if (s->rho_a[n * M + a] < -1e-10 * rho && st == ORC_OK) st = ORC_ERR_NEGATIVE;
     }
     double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
     double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];

@@ -87,17 +87,28 @@ double host_U(const MechConst &mc, int a, double T)
 
 double psi_host(int c, double zeta) { return c == 0 ? 1.0 - zeta : 0.5 * zeta; }
 
-// Rest states of every set at the mean initial density and temperature.
+// Rest states subtracted by mixed-precision storage: every set's rest
+// equilibrium at the mean initial temperature and at the smallest initial
+// density of that set (species: of that species), so that the stored
+// deviations of positive populations stay non-negative and trace species
+// keep float's relative precision.  The energy set uses the rest Grad state
+// of the mean composition at the mean density.
 void choose_references(MechConst &mc, int M, const double *X, const double *T, double P, size_t N)
 {
-    double rho_m[LBMK_MAXM] = {0}, T_m = 0.0, rho_t = 0.0;
+    double rho_min[LBMK_MAXM], rho_m[LBMK_MAXM] = {0}, T_m = 0.0, rho_t = 0.0, rho_tmin = 1e300;
+    for (int a = 0; a < M; ++a) rho_min[a] = 1e300;
     for (size_t n = 0; n < N; ++n) {
         double m = 0.0;
         for (int a = 0; a < M; ++a) m += X[(size_t)a * N + n] * mc.W[a];
         const double rho = P * m / (mc.r_lat * T[n]);
-        for (int a = 0; a < M; ++a) rho_m[a] += rho * X[(size_t)a * N + n] * mc.W[a] / m;
+        for (int a = 0; a < M; ++a) {
+            const double ra = rho * X[(size_t)a * N + n] * mc.W[a] / m;
+            rho_m[a] += ra;
+            if (ra < rho_min[a]) rho_min[a] = ra;
+        }
         T_m += T[n];
         rho_t += rho;
+        if (rho < rho_tmin) rho_tmin = rho;
     }
     for (int a = 0; a < M; ++a) rho_m[a] /= (double)N;
     T_m /= (double)N;
@@ -117,7 +128,7 @@ void choose_references(MechConst &mc, int M, const double *X, const double *T, d
             double v;
             if (s < M) {
                 const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T_m;
-                const double r = s < M - 1 ? rho_m[s] : rho_t;
+                const double r = s < M - 1 ? rho_min[s] : rho_tmin;
                 v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
             } else {
                 const double w = (cx ? 1.0 / 6.0 : 2.0 / 3.0) * (cy ? 1.0 / 6.0 : 2.0 / 3.0) * (cz ? 1.0 / 6.0 : 2.0 / 3.0);

@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a, unsigned mask, d
     for (int s = 0; s < M; ++s) {
         Y[s] = rho_a[s] / rho;
         inv_m += Y[s] * mc.invW[s];
-        neg |= rho_a[s] < 0.0;
+        neg |= rho_a[s] < -1e-10 * rho;      // below rounding noise of trace species
     }
     if (!(rho > 0.0) || !isfinite(rhoE)) flag(a, LBMK_BIT_NONFINITE);
     if (neg) flag(a, LBMK_BIT_NEGATIVE);
