@@ -83,15 +83,17 @@ def _normalise_with_noise(X0: np.ndarray, N: int, seed, amp: float = 1e-3) -> np
     """X0 [M] mean mole fractions -> [M,N] with per-node uniform noise.
 
     Draw order: one array of shape [N, M] (node-major, x fastest, then
-    species) from numpy's PCG64 with the given seed; clip at X_FLOOR and
-    renormalise each node.
+    species) from numpy's PCG64 with the given seed.  The noise perturbs the
+    species present in X0; absent species stay at X_FLOOR (noise on them
+    would make trace densities jump by nine orders of magnitude between
+    neighbouring nodes).  Clip at X_FLOOR and renormalise each node.
     """
     M = X0.shape[0]
     X = np.repeat(X0[:, None], N, axis=1)
     if seed is not None:
         rng = np.random.Generator(np.random.PCG64(seed))
         noise = rng.uniform(-amp, amp, size=(N, M))
-        X = X + noise.T
+        X = X + noise.T * (X0 > 0)[:, None]
     X = np.maximum(X, X_FLOOR)
     X = X / X.sum(axis=0, keepdims=True)
     return np.ascontiguousarray(X)
