@@ -187,6 +187,38 @@ int lbm_get_populations(lbm_ctx *ctx, double *host_out);
  * pop_b); with the T row of macro it is everything a checkpoint needs. */
 void *lbm_state_buffer(lbm_ctx *ctx);
 
+/* One double-precision time step that allocates nothing (the paper has no
+ * counterpart; this is a service for callers).  Some callers cannot call
+ * cudaMalloc where they need to step the lattice: a plugin or callback
+ * running inside another framework that owns every device allocation, a
+ * process whose device allocator is capped or exhausted, or code that must
+ * avoid the implicit synchronisation an allocation can cause.  They can
+ * still pass their own population buffers, so this entry point takes
+ *   pop_in   device, double [M+1][27][N]: post-collision state (input)
+ *   pop_out  device, double [M+1][27][N]: the state one step later (output,
+ *            distinct from pop_in)
+ *   T_io     device, double [N]: starting temperatures for the Newton
+ *            iteration on input; the temperatures of the step's moments on
+ *            output
+ * and keeps the per-node macroscopic record, the x-face ghost planes and the
+ * status word in a fixed device array of LBM_FIXED_SCRATCH_BYTES compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits.  No context (lbm_create) is needed; the species and
+ * mechanism tables are copied to constant memory on every call.
+ * Limits: precision LBM_FP64 only (else LBM_ERR_UNSUPPORTED); the lattice
+ * must fit, 256 + (M+8) N 8 bytes plus, for non-periodic x, 2 (M+1) 27 ny nz
+ * 8 bytes <= LBM_FIXED_SCRATCH_BYTES (e.g. 64^3 nodes with M = 9), else
+ * LBM_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call uses the same array and it keeps the previous call's
+ * contents (the call clears its status word itself), so calls that overlap
+ * on the GPU -- on different streams or host threads -- race and must be
+ * serialised by the caller.  Waits for the stream and returns like
+ * lbm_step. */
+#define LBM_FIXED_SCRATCH_BYTES (64u << 20)
+int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
+                           const double *pop_in, double *pop_out, double *T_io, void *cuda_stream);
+
 /* Frees host state and the status word; never the caller's buffers. */
 int lbm_destroy(lbm_ctx *ctx);
 

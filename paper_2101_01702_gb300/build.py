@@ -15,7 +15,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "liblbm.so"
-SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu"]
+SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_fixed_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1,0 +1,208 @@
+// One double-precision time step whose working memory is a fixed array
+// compiled into this library, for callers that cannot allocate GPU memory.
+//
+// Who needs this: code that runs where cudaMalloc is not available or not
+// allowed at the point of the call -- for example a host callback or a
+// plugin inside another framework that owns every device allocation, a
+// process whose allocator is capped or already exhausted, or a caller that
+// must not trigger an implicit device synchronisation.  Such callers can
+// pass their own population buffers (inputs and outputs) but cannot hand the
+// library the per-node macroscopic record and ghost planes that lbm_step keeps
+// in caller-provided scratch buffers.  Here that scratch lives in
+// g_fixed_scratch, a file-scope device array of LBM_FIXED_SCRATCH_BYTES that
+// every GPU which loads the library keeps until the process exits.
+//
+// The kernels are the same templates as the double-precision unit
+// (lbm_kernels.cuh); this translation unit has its own constant-memory copy
+// of the tables, so it never touches the contexts created by lbm_create.
+#define LBMK_MIXED 0
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+// Device-side scratch.  Layout of one call: [0, 256) status word,
+// [256, 256 + (M+8) N 8) macroscopic record, then the x-face ghost planes.
+static __device__ __align__(256) unsigned char g_fixed_scratch[LBM_FIXED_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_fixed_scratch on the current device.  In host code
+// the symbol name only stands for the array; the address a kernel may use
+// comes from cudaGetSymbolAddress, looked up once per device.
+int scratch_address(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) return LBM_ERR_CUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return LBM_OK;
+}
+
+// Packs the species and mechanism description into the constant-memory
+// record (same layout the kernels of lbm_create contexts read).
+int pack_tables(const lbm_species *sp, const lbm_mechanism *mech, MechConst &mc)
+{
+    const int M = sp->M;
+    memset(&mc, 0, sizeof(mc));
+    if (!sp->W || !sp->D) return LBM_ERR_ARG;
+    if (sp->thermo == LBM_THERMO_CONST_CP && (!sp->cp_R || !sp->h_form)) return LBM_ERR_ARG;
+    if (sp->thermo == LBM_THERMO_POLY7 && !sp->poly7) return LBM_ERR_ARG;
+    if (sp->thermo != LBM_THERMO_CONST_CP && sp->thermo != LBM_THERMO_POLY7) return LBM_ERR_ARG;
+    if (sp->visc_model != LBM_VISC_KINEMATIC && sp->visc_model != LBM_VISC_RELAXATION) return LBM_ERR_ARG;
+    if (!(sp->r_lat > 0) || !(sp->nu > 0) || !(sp->Pr > 0)) return LBM_ERR_ARG;
+    if (mech->R < 0 || mech->R > LBMK_MAXR) return LBM_ERR_ARG;
+    if (mech->R > 0 && (!mech->nu_f || !mech->nu_r || !mech->log_A || !mech->b || !mech->theta || !mech->rtype ||
+                        !mech->reversible || !(mech->T_ref > 0)))
+        return LBM_ERR_ARG;
+    mc.M = M;
+    mc.R = mech->R;
+    mc.thermo = sp->thermo;
+    mc.visc_model = sp->visc_model;
+    mc.T0 = sp->T0;
+    mc.nu = sp->nu;
+    mc.Pr = sp->Pr;
+    mc.r_lat = sp->r_lat;
+    for (int a = 0; a < M; ++a) {
+        if (!(sp->W[a] > 0)) return LBM_ERR_ARG;
+        mc.W[a] = sp->W[a];
+        mc.invW[a] = 1.0 / sp->W[a];
+        mc.Ra[a] = sp->r_lat / sp->W[a];
+        if (sp->thermo == LBM_THERMO_CONST_CP) {
+            mc.cpR[a] = sp->cp_R[a];
+            mc.cv[a] = (sp->cp_R[a] - 1.0) * mc.Ra[a];
+            mc.U0[a] = sp->h_form[a] - mc.Ra[a] * sp->T0;
+        } else {
+            for (int k = 0; k < 7; ++k) mc.poly[a][k] = sp->poly7[7 * a + k];
+        }
+        for (int b = 0; b < M; ++b) {
+            if (a == b) continue;
+            const double D = sp->D[M * a + b];
+            if (!(D > 0) || D != sp->D[M * b + a]) return LBM_ERR_ARG;
+            mc.inv_WWD[a][b] = 1.0 / (sp->W[a] * sp->W[b] * D);
+            mc.inv_WWD_f[a][b] = (float)mc.inv_WWD[a][b];
+        }
+    }
+    mc.log_T_ref = mech->R > 0 ? log(mech->T_ref) : 0.0;
+    bool need_P0 = false;
+    for (int k = 0; k < mech->R; ++k) {
+        const int t = mech->rtype[k];
+        if (t < 0 || t > 2 || (t != 0 && !mech->eff) || (t == 2 && !mech->low)) return LBM_ERR_ARG;
+        mc.rtype[k] = t;
+        mc.rev[k] = mech->reversible[k] ? 1 : 0;
+        need_P0 |= mc.rev[k] != 0;
+        mc.log_A[k] = mech->log_A[k];
+        mc.b[k] = mech->b[k];
+        mc.theta[k] = mech->theta[k];
+        if (t == 2)
+            for (int d = 0; d < 3; ++d) mc.low[k][d] = mech->low[3 * k + d];
+        int nr = 0, np = 0, nd = 0;
+        double dn = 0.0;
+        for (int a = 0; a < M; ++a) {
+            const int f = mech->nu_f[M * k + a], g = mech->nu_r[M * k + a];
+            if (f < 0 || g < 0) return LBM_ERR_ARG;
+            for (int j = 0; j < f; ++j) { if (nr >= 3) return LBM_ERR_ARG; mc.reac[k][nr++] = a; }
+            for (int j = 0; j < g; ++j) { if (np >= 3) return LBM_ERR_ARG; mc.prod[k][np++] = a; }
+            if (g != f) {
+                if (nd >= 6) return LBM_ERR_ARG;
+                mc.dnu_sp[k][nd] = a;
+                mc.dnu_v[k][nd++] = g - f;
+                dn += g - f;
+            }
+            if (t != 0) mc.eff[k][a] = mech->eff[M * k + a];
+        }
+        if (nr == 0) return LBM_ERR_ARG;
+        mc.nreac[k] = nr;
+        mc.nprod[k] = np;
+        mc.ndnu[k] = nd;
+        mc.dn[k] = dn;
+    }
+    if (need_P0) {
+        if (!(mech->P0 > 0)) return LBM_ERR_ARG;
+        mc.log_P0_over_r = log(mech->P0 / sp->r_lat);
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
+                                      const double *pop_in, double *pop_out, double *T_io, void *cuda_stream)
+{
+    if (!lat || !sp || !mech || !pop_in || !pop_out || !T_io || pop_in == pop_out) return LBM_ERR_ARG;
+    if (lat->precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
+    if (lat->bc_x != LBM_BC_PERIODIC && lat->bc_x != LBM_BC_EQ_ZEROGRAD_U0LEFT) return LBM_ERR_ARG;
+    if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || sp->M < 2 || sp->M > LBMK_MAXM) return LBM_ERR_ARG;
+    if (sp->M != 2 && sp->M != 3 && sp->M != 9) return LBM_ERR_UNSUPPORTED;
+    const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
+    const size_t S = (size_t)sp->M + 1;
+    const size_t macro_bytes = (size_t)(sp->M + MAC_Y) * N * sizeof(double);
+    const size_t ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : 2 * S * LBMK_Q * (size_t)lat->ny * lat->nz * sizeof(double);
+    if (N > (size_t)0x7fffffff || 256 + macro_bytes + ghost_bytes > (size_t)LBM_FIXED_SCRATCH_BYTES)
+        return LBM_ERR_ARG;     // lattice too large for the fixed scratch array
+    MechConst mc;
+    int st = pack_tables(sp, mech, mc);
+    if (st != LBM_OK) return st;
+    void *base = nullptr;
+    st = scratch_address(&base);
+    if (st != LBM_OK) return st;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    unsigned char *scratch = (unsigned char *)base;
+
+    StepArgs a;
+    a.slot = 0;
+    a.M = sp->M;
+    a.nx = lat->nx;
+    a.ny = lat->ny;
+    a.nz = lat->nz;
+    a.N = (int)N;
+    a.bc_x = lat->bc_x;
+    a.src = pop_in;
+    a.dst = pop_out;
+    a.status = (unsigned *)scratch;
+    a.macro = (double *)(scratch + 256);
+    a.ghost = ghost_bytes ? (void *)(scratch + 256 + macro_bytes) : nullptr;
+    a.stream = stream;
+
+    // The array keeps the previous call's contents: clear the status word;
+    // the temperature row is the Newton starting point and comes from T_io;
+    // every other row and the ghost planes are written before they are read.
+    if (cudaMemcpyToSymbolAsync(c_mech, &mc, sizeof(MechConst), 0, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaMemsetAsync(a.status, 0, 256, stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemcpyAsync(a.macro + (size_t)MAC_T * N, T_io, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
+        cudaSuccess)
+        return LBM_ERR_CUDA;
+    int e;
+    switch (sp->M) {
+    case 2: e = run_step<2>(a, nullptr); break;
+    case 3: e = run_step<3>(a, nullptr); break;
+    default: e = run_step<9>(a, nullptr); break;
+    }
+    if (e) return LBM_ERR_CUDA;
+    if (cudaMemcpyAsync(T_io, a.macro + (size_t)MAC_T * N, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
+        cudaSuccess)
+        return LBM_ERR_CUDA;
+    unsigned bits = 0;
+    if (cudaMemcpyAsync(&bits, a.status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (bits & LBMK_BIT_NONFINITE) return LBM_ERR_NONFINITE;
+    if (bits & LBMK_BIT_NEWTON) return LBM_ERR_NEWTON;
+    if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
+    if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
+    return LBM_OK;
+}

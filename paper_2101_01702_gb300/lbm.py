@@ -74,12 +74,14 @@ _lib.lbm_get_populations.argtypes = [C.c_void_p, _dp]
 _lib.lbm_state_buffer.argtypes = [C.c_void_p]
 _lib.lbm_state_buffer.restype = C.c_void_p
 _lib.lbm_destroy.argtypes = [C.c_void_p]
+_lib.lbm_step_fixed_scratch.argtypes = [C.POINTER(lbm_lattice), C.POINTER(lbm_species), C.POINTER(lbm_mechanism),
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.lbm_strerror.argtypes = [C.c_int]
 _lib.lbm_strerror.restype = C.c_char_p
 
 EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
-            "lbm_strerror"]
+            "lbm_strerror", "lbm_step_fixed_scratch"]
 
 
 def library_path() -> str:
@@ -155,6 +157,13 @@ def lbm_state_buffer(ctx) -> int:
 
 def lbm_destroy(ctx) -> int:
     return _lib.lbm_destroy(ctx)
+
+
+def lbm_step_fixed_scratch(lat, sp, mech, pop_in_ptr: int, pop_out_ptr: int, T_io_ptr: int, stream: int) -> int:
+    """One double-precision step with the library's fixed device scratch
+    array (no allocation); see include/lbm.h for the limits."""
+    return _lib.lbm_step_fixed_scratch(C.byref(lat), C.byref(sp), C.byref(mech), C.c_void_p(pop_in_ptr),
+                                       C.c_void_p(pop_out_ptr), C.c_void_p(T_io_ptr), C.c_void_p(stream))
 
 
 def lbm_strerror(st: int) -> str:
