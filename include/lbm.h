@@ -123,8 +123,10 @@ typedef struct {
  *   pop_a, pop_b  two population buffers, layout [M+1 sets][27][N], double
  *                 (LBM_FP64) or float deviations (LBM_MIXED); they swap roles
  *                 every step.  Must be distinct and 16-byte aligned.
- *   macro         per-node fields, double [(M+8)][N]: T, 1/omega - 1/2,
- *                 Phi (3), G (3), Y (M).
+ *   macro         per-node record: a row of doubles (temperature) then
+ *                 21 + 7M rows of the storage type ([rows][N]): the
+ *                 moments, relaxation rates, diffusion velocities,
+ *                 production rates and gradient inputs of the current step.
  *   ghost         x-face ghost populations [2][M+1][27][ny*nz] in the
  *                 storage type; may be NULL for periodic x. */
 typedef struct {
@@ -206,9 +208,9 @@ void *lbm_state_buffer(lbm_ctx *ctx);
  * process exits.  No context (lbm_create) is needed; the species and
  * mechanism tables are copied to constant memory on every call.
  * Limits: precision LBM_FP64 only (else LBM_ERR_UNSUPPORTED); the lattice
- * must fit, 256 + (M+8) N 8 bytes plus, for non-periodic x, 2 (M+1) 27 ny nz
- * 8 bytes <= LBM_FIXED_SCRATCH_BYTES (e.g. 64^3 nodes with M = 9), else
- * LBM_ERR_ARG.  The first call on a device looks up the array's device
+ * must fit, 256 + (22 + 7M) N 8 bytes plus, for non-periodic x,
+ * 2 (M+1) 27 ny nz 8 bytes <= LBM_FIXED_SCRATCH_BYTES (e.g. 40^3 nodes
+ * with M = 9, 64^3 with M = 3), else LBM_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call uses the same array and it keeps the previous call's
  * contents (the call clears its status word itself), so calls that overlap

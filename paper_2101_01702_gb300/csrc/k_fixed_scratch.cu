@@ -23,9 +23,10 @@
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_pack.h"
 
-// Device-side scratch.  Layout of one call: [0, 256) status word,
-// [256, 256 + (M+8) N 8) macroscopic record, then the x-face ghost planes.
+// Device-side scratch.  Layout of one call: [0, 256) status word, then the
+// macroscopic record (8 N (22 + 7M) bytes), then the x-face ghost planes.
 static __device__ __align__(256) unsigned char g_fixed_scratch[LBM_FIXED_SCRATCH_BYTES];
 
 namespace {
@@ -52,91 +53,6 @@ int scratch_address(void **out)
     return LBM_OK;
 }
 
-// Packs the species and mechanism description into the constant-memory
-// record (same layout the kernels of lbm_create contexts read).
-int pack_tables(const lbm_species *sp, const lbm_mechanism *mech, MechConst &mc)
-{
-    const int M = sp->M;
-    memset(&mc, 0, sizeof(mc));
-    if (!sp->W || !sp->D) return LBM_ERR_ARG;
-    if (sp->thermo == LBM_THERMO_CONST_CP && (!sp->cp_R || !sp->h_form)) return LBM_ERR_ARG;
-    if (sp->thermo == LBM_THERMO_POLY7 && !sp->poly7) return LBM_ERR_ARG;
-    if (sp->thermo != LBM_THERMO_CONST_CP && sp->thermo != LBM_THERMO_POLY7) return LBM_ERR_ARG;
-    if (sp->visc_model != LBM_VISC_KINEMATIC && sp->visc_model != LBM_VISC_RELAXATION) return LBM_ERR_ARG;
-    if (!(sp->r_lat > 0) || !(sp->nu > 0) || !(sp->Pr > 0)) return LBM_ERR_ARG;
-    if (mech->R < 0 || mech->R > LBMK_MAXR) return LBM_ERR_ARG;
-    if (mech->R > 0 && (!mech->nu_f || !mech->nu_r || !mech->log_A || !mech->b || !mech->theta || !mech->rtype ||
-                        !mech->reversible || !(mech->T_ref > 0)))
-        return LBM_ERR_ARG;
-    mc.M = M;
-    mc.R = mech->R;
-    mc.thermo = sp->thermo;
-    mc.visc_model = sp->visc_model;
-    mc.T0 = sp->T0;
-    mc.nu = sp->nu;
-    mc.Pr = sp->Pr;
-    mc.r_lat = sp->r_lat;
-    for (int a = 0; a < M; ++a) {
-        if (!(sp->W[a] > 0)) return LBM_ERR_ARG;
-        mc.W[a] = sp->W[a];
-        mc.invW[a] = 1.0 / sp->W[a];
-        mc.Ra[a] = sp->r_lat / sp->W[a];
-        if (sp->thermo == LBM_THERMO_CONST_CP) {
-            mc.cpR[a] = sp->cp_R[a];
-            mc.cv[a] = (sp->cp_R[a] - 1.0) * mc.Ra[a];
-            mc.U0[a] = sp->h_form[a] - mc.Ra[a] * sp->T0;
-        } else {
-            for (int k = 0; k < 7; ++k) mc.poly[a][k] = sp->poly7[7 * a + k];
-        }
-        for (int b = 0; b < M; ++b) {
-            if (a == b) continue;
-            const double D = sp->D[M * a + b];
-            if (!(D > 0) || D != sp->D[M * b + a]) return LBM_ERR_ARG;
-            mc.inv_WWD[a][b] = 1.0 / (sp->W[a] * sp->W[b] * D);
-            mc.inv_WWD_f[a][b] = (float)mc.inv_WWD[a][b];
-        }
-    }
-    mc.log_T_ref = mech->R > 0 ? log(mech->T_ref) : 0.0;
-    bool need_P0 = false;
-    for (int k = 0; k < mech->R; ++k) {
-        const int t = mech->rtype[k];
-        if (t < 0 || t > 2 || (t != 0 && !mech->eff) || (t == 2 && !mech->low)) return LBM_ERR_ARG;
-        mc.rtype[k] = t;
-        mc.rev[k] = mech->reversible[k] ? 1 : 0;
-        need_P0 |= mc.rev[k] != 0;
-        mc.log_A[k] = mech->log_A[k];
-        mc.b[k] = mech->b[k];
-        mc.theta[k] = mech->theta[k];
-        if (t == 2)
-            for (int d = 0; d < 3; ++d) mc.low[k][d] = mech->low[3 * k + d];
-        int nr = 0, np = 0, nd = 0;
-        double dn = 0.0;
-        for (int a = 0; a < M; ++a) {
-            const int f = mech->nu_f[M * k + a], g = mech->nu_r[M * k + a];
-            if (f < 0 || g < 0) return LBM_ERR_ARG;
-            for (int j = 0; j < f; ++j) { if (nr >= 3) return LBM_ERR_ARG; mc.reac[k][nr++] = a; }
-            for (int j = 0; j < g; ++j) { if (np >= 3) return LBM_ERR_ARG; mc.prod[k][np++] = a; }
-            if (g != f) {
-                if (nd >= 6) return LBM_ERR_ARG;
-                mc.dnu_sp[k][nd] = a;
-                mc.dnu_v[k][nd++] = g - f;
-                dn += g - f;
-            }
-            if (t != 0) mc.eff[k][a] = mech->eff[M * k + a];
-        }
-        if (nr == 0) return LBM_ERR_ARG;
-        mc.nreac[k] = nr;
-        mc.nprod[k] = np;
-        mc.ndnu[k] = nd;
-        mc.dn[k] = dn;
-    }
-    if (need_P0) {
-        if (!(mech->P0 > 0)) return LBM_ERR_ARG;
-        mc.log_P0_over_r = log(mech->P0 / sp->r_lat);
-    }
-    return LBM_OK;
-}
-
 }  // namespace
 
 extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
@@ -149,12 +65,12 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     if (sp->M != 2 && sp->M != 3 && sp->M != 9) return LBM_ERR_UNSUPPORTED;
     const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
     const size_t S = (size_t)sp->M + 1;
-    const size_t macro_bytes = (size_t)(sp->M + MAC_Y) * N * sizeof(double);
+    const size_t macro_bytes = macro_bytes_for(sp->M, N, sizeof(double));
     const size_t ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : 2 * S * LBMK_Q * (size_t)lat->ny * lat->nz * sizeof(double);
     if (N > (size_t)0x7fffffff || 256 + macro_bytes + ghost_bytes > (size_t)LBM_FIXED_SCRATCH_BYTES)
         return LBM_ERR_ARG;     // lattice too large for the fixed scratch array
     MechConst mc;
-    int st = pack_tables(sp, mech, mc);
+    int st = lbm_pack_tables(sp, mech, mc);
     if (st != LBM_OK) return st;
     void *base = nullptr;
     st = scratch_address(&base);
@@ -183,7 +99,7 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     if (cudaMemcpyToSymbolAsync(c_mech, &mc, sizeof(MechConst), 0, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return LBM_ERR_CUDA;
     if (cudaMemsetAsync(a.status, 0, 256, stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (cudaMemcpyAsync(a.macro + (size_t)MAC_T * N, T_io, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
+    if (cudaMemcpyAsync(a.macro + (size_t)DR_T * N, T_io, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
         cudaSuccess)
         return LBM_ERR_CUDA;
     int e;
@@ -193,7 +109,7 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     default: e = run_step<9>(a, nullptr); break;
     }
     if (e) return LBM_ERR_CUDA;
-    if (cudaMemcpyAsync(T_io, a.macro + (size_t)MAC_T * N, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
+    if (cudaMemcpyAsync(T_io, a.macro + (size_t)DR_T * N, N * sizeof(double), cudaMemcpyDeviceToDevice, stream) !=
         cudaSuccess)
         return LBM_ERR_CUDA;
     unsigned bits = 0;

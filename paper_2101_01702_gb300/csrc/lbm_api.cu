@@ -12,6 +12,7 @@
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
+#include "lbm_pack.h"
 
 struct lbm_ctx {
     lbm_lattice lat;
@@ -74,25 +75,13 @@ StepArgs args_of(const lbm_ctx *c)
     return a;
 }
 
-// Host evaluation of the thermodynamic functions, used only to choose the
-// rest states that mixed-precision storage subtracts.
-double host_U(const MechConst &mc, int a, double T)
-{
-    if (mc.thermo == 0) return mc.U0[a] + mc.cv[a] * (T - mc.T0);
-    const double *p = mc.poly[a];
-    const double h = p[0] * T + p[1] * T * T / 2 + p[2] * T * T * T / 3 + p[3] * T * T * T * T / 4 +
-                     p[4] * T * T * T * T * T / 5 + p[5];
-    return mc.Ra[a] * (h - T);
-}
-
 double psi_host(int c, double zeta) { return c == 0 ? 1.0 - zeta : 0.5 * zeta; }
 
-// Rest states subtracted by mixed-precision storage: every set's rest
-// equilibrium at the mean initial temperature and at the smallest initial
-// density of that set (species: of that species), so that the stored
-// deviations of positive populations stay non-negative and trace species
-// keep float's relative precision.  The energy set uses the rest Grad state
-// of the mean composition at the mean density.
+// Rest states subtracted by mixed-precision storage of the moving
+// populations of the species and mixture sets: each set's rest equilibrium
+// at the mean initial temperature and at the smallest initial density of
+// that set, so that the stored deviations of positive populations stay
+// non-negative and trace species keep float's relative precision.
 void choose_references(MechConst &mc, int M, const double *X, const double *T, double P, size_t N)
 {
     double rho_min[LBMK_MAXM], rho_m[LBMK_MAXM] = {0}, T_m = 0.0, rho_t = 0.0, rho_tmin = 1e300;
@@ -110,38 +99,19 @@ void choose_references(MechConst &mc, int M, const double *X, const double *T, d
         rho_t += rho;
         if (rho < rho_tmin) rho_tmin = rho;
     }
-    for (int a = 0; a < M; ++a) rho_m[a] /= (double)N;
     T_m /= (double)N;
     rho_t /= (double)N;
-    double inv_m = 0.0, Umix = 0.0;
-    for (int a = 0; a < M; ++a) {
-        inv_m += rho_m[a] / rho_t / mc.W[a];
-        Umix += rho_m[a] / rho_t * host_U(mc, a, T_m);
-    }
+    double inv_m = 0.0;
+    for (int a = 0; a < M; ++a) inv_m += rho_m[a] / (double)N / rho_t / mc.W[a];
     const double Rm = mc.r_lat * inv_m;
-    const double Hmix = Umix + Rm * T_m;
-    const double rhoE = rho_t * Umix, Pr = rho_t * Rm * T_m;
-    for (int s = 0; s <= M; ++s) {
-        double m0 = 0.0, m2 = 0.0;
+    for (int s = 0; s < M; ++s)
         for (int i = 0; i < LBMK_Q; ++i) {
             const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
-            double v;
-            if (s < M) {
-                const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T_m;
-                const double r = s < M - 1 ? rho_min[s] : rho_tmin;
-                v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
-            } else {
-                const double w = (cx ? 1.0 / 6.0 : 2.0 / 3.0) * (cy ? 1.0 / 6.0 : 2.0 / 3.0) * (cz ? 1.0 / 6.0 : 2.0 / 3.0);
-                const int c2 = cx * cx + cy * cy + cz * cz;
-                v = w * (rhoE + 4.5 * (Hmix * Pr - rhoE / 3.0) * (c2 - 1.0));
-            }
-            mc.ref[s][i] = (float)v;
-            m0 += (double)mc.ref[s][i];
-            m2 += (double)mc.ref[s][i] * (double)(cx * cx);
+            const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T_m;
+            const double r = s < M - 1 ? rho_min[s] : rho_tmin;
+            const double v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
+            mc.ref[s][i] = i == 13 ? 0.0f : (float)v;     // rest populations are stored in double
         }
-        mc.ref_m0[s] = m0;
-        mc.ref_m2[s] = m2;
-    }
 }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
@@ -159,9 +129,9 @@ int lbm_buffer_sizes(const lbm_lattice *lat, const lbm_species *sp, size_t *pop_
     const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
     const size_t S = (size_t)sp->M + 1;
     const size_t st = store_size(lat->precision);
-    if (pop_bytes) *pop_bytes = S * LBMK_Q * N * st;
-    if (macro_bytes) *macro_bytes = (size_t)(sp->M + MAC_Y) * N * sizeof(double);
-    if (ghost_bytes) *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : 2 * S * LBMK_Q * (size_t)lat->ny * lat->nz * st;
+    if (pop_bytes) *pop_bytes = pop_bytes_for((int)S, N, lat->precision == LBM_MIXED);
+    if (macro_bytes) *macro_bytes = macro_bytes_for(sp->M, N, st);
+    if (ghost_bytes) *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : ghost_bytes_for((int)S, (size_t)lat->ny * lat->nz);
     return LBM_OK;
 }
 
@@ -179,93 +149,14 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     if (N > (size_t)0x7fffffff) return LBM_ERR_ARG;
     const int M = sp->M;
     if (!supported_M(M)) return LBM_ERR_UNSUPPORTED;
-    if (!sp->W || !sp->D) return LBM_ERR_ARG;
-    if (sp->thermo == LBM_THERMO_CONST_CP && (!sp->cp_R || !sp->h_form)) return LBM_ERR_ARG;
-    if (sp->thermo == LBM_THERMO_POLY7 && !sp->poly7) return LBM_ERR_ARG;
-    if (sp->thermo != LBM_THERMO_CONST_CP && sp->thermo != LBM_THERMO_POLY7) return LBM_ERR_ARG;
-    if (sp->visc_model != LBM_VISC_KINEMATIC && sp->visc_model != LBM_VISC_RELAXATION) return LBM_ERR_ARG;
-    if (!(sp->r_lat > 0) || !(sp->nu > 0) || !(sp->Pr > 0)) return LBM_ERR_ARG;
-    if (mech->R < 0 || mech->R > LBMK_MAXR) return LBM_ERR_ARG;
-    if (mech->R > 0 && (!mech->nu_f || !mech->nu_r || !mech->log_A || !mech->b || !mech->theta || !mech->rtype ||
-                        !mech->reversible))
-        return LBM_ERR_ARG;
     if (!bufs->pop_a || !bufs->pop_b || bufs->pop_a == bufs->pop_b || !bufs->macro) return LBM_ERR_ARG;
     if (bufs->pop_bytes < need_pop || bufs->macro_bytes < need_mac) return LBM_ERR_ARG;
     if (need_gh && (!bufs->ghost || bufs->ghost_bytes < need_gh)) return LBM_ERR_ARG;
     if (((uintptr_t)bufs->pop_a | (uintptr_t)bufs->pop_b | (uintptr_t)bufs->macro) & 15u) return LBM_ERR_ARG;
 
     MechConst mc;
-    memset(&mc, 0, sizeof(mc));
-    mc.M = M;
-    mc.R = mech->R;
-    mc.thermo = sp->thermo;
-    mc.visc_model = sp->visc_model;
-    mc.T0 = sp->T0;
-    mc.nu = sp->nu;
-    mc.Pr = sp->Pr;
-    mc.r_lat = sp->r_lat;
-    for (int a = 0; a < M; ++a) {
-        if (!(sp->W[a] > 0)) return LBM_ERR_ARG;
-        mc.W[a] = sp->W[a];
-        mc.invW[a] = 1.0 / sp->W[a];
-        mc.Ra[a] = sp->r_lat / sp->W[a];
-        if (sp->thermo == LBM_THERMO_CONST_CP) {
-            mc.cpR[a] = sp->cp_R[a];
-            mc.cv[a] = (sp->cp_R[a] - 1.0) * mc.Ra[a];
-            mc.U0[a] = sp->h_form[a] - mc.Ra[a] * sp->T0;
-        } else {
-            for (int k = 0; k < 7; ++k) mc.poly[a][k] = sp->poly7[7 * a + k];
-        }
-        for (int b = 0; b < M; ++b) {
-            const double D = sp->D[M * a + b];
-            if (a != b) {
-                if (!(D > 0) || D != sp->D[M * b + a]) return LBM_ERR_ARG;
-                mc.inv_WWD[a][b] = 1.0 / (sp->W[a] * sp->W[b] * D);
-                mc.inv_WWD_f[a][b] = (float)mc.inv_WWD[a][b];
-            }
-        }
-    }
-    if (mech->R > 0 && !(mech->T_ref > 0)) return LBM_ERR_ARG;
-    mc.log_T_ref = mech->R > 0 ? log(mech->T_ref) : 0.0;
-    bool need_P0 = false;
-    for (int k = 0; k < mech->R; ++k) {
-        const int t = mech->rtype[k];
-        if (t < 0 || t > 2) return LBM_ERR_ARG;
-        if (t != 0 && !mech->eff) return LBM_ERR_ARG;
-        if (t == 2 && !mech->low) return LBM_ERR_ARG;
-        mc.rtype[k] = t;
-        mc.rev[k] = mech->reversible[k] ? 1 : 0;
-        need_P0 |= mc.rev[k] != 0;
-        mc.log_A[k] = mech->log_A[k];
-        mc.b[k] = mech->b[k];
-        mc.theta[k] = mech->theta[k];
-        if (t == 2)
-            for (int d = 0; d < 3; ++d) mc.low[k][d] = mech->low[3 * k + d];
-        int nr = 0, np = 0, nd = 0;
-        double dn = 0.0;
-        for (int a = 0; a < M; ++a) {
-            const int f = mech->nu_f[M * k + a], g = mech->nu_r[M * k + a];
-            if (f < 0 || g < 0) return LBM_ERR_ARG;
-            for (int j = 0; j < f; ++j) { if (nr >= 3) return LBM_ERR_ARG; mc.reac[k][nr++] = a; }
-            for (int j = 0; j < g; ++j) { if (np >= 3) return LBM_ERR_ARG; mc.prod[k][np++] = a; }
-            if (g != f) {
-                if (nd >= 6) return LBM_ERR_ARG;
-                mc.dnu_sp[k][nd] = a;
-                mc.dnu_v[k][nd++] = g - f;
-                dn += g - f;
-            }
-            if (t != 0) mc.eff[k][a] = mech->eff[M * k + a];
-        }
-        if (nr == 0) return LBM_ERR_ARG;
-        mc.nreac[k] = nr;
-        mc.nprod[k] = np;
-        mc.ndnu[k] = nd;
-        mc.dn[k] = dn;
-    }
-    if (need_P0) {
-        if (!(mech->P0 > 0)) return LBM_ERR_ARG;
-        mc.log_P0_over_r = log(mech->P0 / sp->r_lat);
-    }
+    r = lbm_pack_tables(sp, mech, mc);
+    if (r != LBM_OK) return r;
 
     int slot = -1;
     {
@@ -469,16 +360,26 @@ int lbm_get_populations(lbm_ctx *c, double *host_out)
     if (st != LBM_OK) return st;
     if (c->lat.precision == LBM_FP64)
         return check_cuda(cudaMemcpy(host_out, c->buf[c->cur], cnt * sizeof(double), cudaMemcpyDeviceToHost));
-    float *tmp = (float *)malloc(cnt * sizeof(float));
-    if (!tmp) return LBM_ERR_ARG;
-    st = check_cuda(cudaMemcpy(tmp, c->buf[c->cur], cnt * sizeof(float), cudaMemcpyDeviceToHost));
+    const size_t M = (size_t)c->M, N = (size_t)c->N;
+    float *mov = (float *)malloc(M * LBMK_Q * N * sizeof(float));
+    double *dbl = (double *)malloc((M + LBMK_Q) * N * sizeof(double));   // rest [M][N], then g [27][N]
+    if (!mov || !dbl) { free(mov); free(dbl); return LBM_ERR_ARG; }
+    st = check_cuda(cudaMemcpy(mov, c->buf[c->cur], M * LBMK_Q * N * sizeof(float), cudaMemcpyDeviceToHost));
     if (st == LBM_OK)
-        for (int s = 0; s < c->S; ++s)
+        st = check_cuda(cudaMemcpy(dbl, (const char *)c->buf[c->cur] + pop_float_bytes(c->M, N),
+                                   (M + LBMK_Q) * N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (st == LBM_OK)
+        for (size_t s = 0; s <= M; ++s)
             for (int i = 0; i < LBMK_Q; ++i) {
-                const size_t base = ((size_t)s * LBMK_Q + i) * c->N;
-                for (int n = 0; n < c->N; ++n) host_out[base + n] = (double)tmp[base + n] + (double)c->mc.ref[s][i];
+                double *o = host_out + (s * LBMK_Q + i) * N;
+                for (size_t n = 0; n < N; ++n) {
+                    if (s == M) o[n] = dbl[M * N + (size_t)i * N + n];
+                    else if (i == 13) o[n] = dbl[s * N + n];
+                    else o[n] = (double)mov[(s * LBMK_Q + i) * N + n] + (double)c->mc.ref[s][i];
+                }
             }
-    free(tmp);
+    free(mov);
+    free(dbl);
     return st;
 }
 

@@ -1,5 +1,5 @@
-// Internal declarations shared by the C-ABI translation unit and the two
-// kernel translation units (double and mixed precision).
+// Internal declarations shared by the C-ABI translation unit and the kernel
+// translation units (double, mixed precision, fixed scratch).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,42 +18,93 @@
 #define LBMK_BIT_NEGATIVE 4u
 #define LBMK_BIT_PIVOT 8u
 
-// Row offsets of the per-node macroscopic record (double, [rows][N]).
-#define MAC_T 0
-#define MAC_NUP 1
-#define MAC_PHI 2
-#define MAC_G 5
-#define MAC_Y 8
+// Per-node record in the macro buffer: macro_double_rows(M) rows of
+// doubles, then rec_rows(M).total rows of the storage type (float in mixed
+// precision, double otherwise), each row [N].
+// Double rows:
+//   DR_T      temperature (Newton starting point and result)
+//   DR_FEQ0   rest-direction equilibrium of the species and mixture sets (M)
+//   DR_GE     rho E            DR_GQ  q^eq (3)       DR_GR  R^eq - rho E theta I (6: xx yy zz xy xz yz)
+//   DR_GTR    tr(R^eq - rho E theta I) / 3
+// Storage-type rows:
+//   nup  1/omega - 1/2      phi  Phi (3)        g    G (3)
+//   y    Y_a (M)            rho  rho            u    u (3)
+//   du   du_a (3M, a-major) wd   rho_dot_a (M)  beta beta_a (M)
+//   kappa m R_U T           rt   R T            om   omega      om1 omega_1
+//   p    P                  dq   (omega - omega_1)(q* - q^eq) without the grad-Y part (3)
+//   h    H_a (M)
+#define DR_T 0
+#define DR_FEQ0 1
+__host__ __device__ constexpr int dr_ge(int M) { return M + 1; }
+__host__ __device__ constexpr int dr_gq(int M) { return M + 2; }
+__host__ __device__ constexpr int dr_gr(int M) { return M + 5; }
+__host__ __device__ constexpr int dr_gtr(int M) { return M + 11; }
+__host__ __device__ constexpr int macro_double_rows(int M) { return M + 12; }
+struct RecRows {
+    int nup, phi, g, y, rho, u, du, wd, beta, kappa, rt, om, om1, p, dq, h, total;
+};
+__host__ __device__ constexpr RecRows rec_rows(int M)
+{
+    return RecRows{0, 1, 4, 7, 7 + M, 8 + M, 11 + M, 11 + 4 * M, 11 + 5 * M, 11 + 6 * M, 12 + 6 * M, 13 + 6 * M,
+                   14 + 6 * M, 15 + 6 * M, 16 + 6 * M, 19 + 6 * M, 19 + 7 * M};
+}
+// Bytes of the macro buffer for N nodes, M species and a storage element size.
+__host__ __device__ constexpr size_t macro_bytes_for(int M, size_t N, size_t real_size)
+{
+    return (size_t)macro_double_rows(M) * N * sizeof(double) + (size_t)rec_rows(M).total * N * real_size;
+}
+
+// Population buffer.
+//   Double precision: [S][27][N] doubles (S = M + 1 sets: species 0..M-2,
+//   mixture f, energy g).
+//   Mixed precision: the M species and mixture sets as float deviations
+//   [M][27][N] (the rest slot unused), then at a 16-byte boundary their rest
+//   populations [M][N] in double, then the energy set g [27][N] in double.
+//   On the low-temperature lattice the rest population carries most of a
+//   set's mass (a factor 1 - R T per axis), and the energy populations fix
+//   the temperature that the Arrhenius rates amplify, so these stay double.
+// Ghost planes (x faces): [2][S][27][ny nz] doubles in both precisions.
+__host__ __device__ constexpr size_t pop_float_bytes(int M, size_t N) { return ((size_t)M * 27 * N * 4 + 15) & ~(size_t)15; }
+__host__ __device__ constexpr size_t pop_bytes_for(int S, size_t N, bool mixed)
+{
+    return mixed ? pop_float_bytes(S - 1, N) + (size_t)(S - 1) * N * sizeof(double) + (size_t)27 * N * sizeof(double)
+                 : (size_t)S * 27 * N * sizeof(double);
+}
+__host__ __device__ constexpr size_t ghost_bytes_for(int S, size_t plane) { return 2 * (size_t)S * 27 * plane * sizeof(double); }
 
 // Everything the kernels read from constant memory for one context.
+//   H_a(T) = sum_k hco[a][k] T^(k+1) (k = 0..4) + hco[a][5]
+//   U_a(T) = sum_k uco[a][k] T^k (k = 0..5)              (U_a = H_a - R_a T)
+//   g_a/(R_U T) = gco0 (1 - ln T) + gco1 T + gco2 T^2 + gco3 T^3 + gco4 T^4
+//                 + gco5 / T + gco6
+// Both the constant-cp and the 7-coefficient thermodynamics map onto these.
 struct MechConst {
-    int M, R, thermo, visc_model;
-    double T0, nu, Pr, r_lat, log_T_ref, log_P0_over_r;
+    int M, R;
+    int visc_model;
+    double T0, nu, Pr, r_lat, log_T_ref, P0_over_r;
     double W[LBMK_MAXM], invW[LBMK_MAXM], Ra[LBMK_MAXM];
-    double U0[LBMK_MAXM], cv[LBMK_MAXM], cpR[LBMK_MAXM];     // constant-cp thermodynamics
-    double poly[LBMK_MAXM][7];                              // polynomial thermodynamics
-    double inv_WWD[LBMK_MAXM][LBMK_MAXM];                   // 1 / (W_a W_b D_ab)
+    float Ra_f[LBMK_MAXM];
+    double hco[LBMK_MAXM][6], uco[LBMK_MAXM][6], gco[LBMK_MAXM][7];
+    double inv_WWD[LBMK_MAXM][LBMK_MAXM];                   // 1 / (W_a W_b D_ab), 0 on the diagonal
     float inv_WWD_f[LBMK_MAXM][LBMK_MAXM];
     int rtype[LBMK_MAXR], rev[LBMK_MAXR];
     int nreac[LBMK_MAXR], nprod[LBMK_MAXR];
     int reac[LBMK_MAXR][3], prod[LBMK_MAXR][3];             // species of each molecule
-    int ndnu[LBMK_MAXR], dnu_sp[LBMK_MAXR][6], dnu_v[LBMK_MAXR][6];
-    double dn[LBMK_MAXR];
-    double log_A[LBMK_MAXR], b[LBMK_MAXR], theta[LBMK_MAXR], low[LBMK_MAXR][3];
+    int dn[LBMK_MAXR];                                      // sum of product minus reactant coefficients
+    double log_A[LBMK_MAXR], b[LBMK_MAXR], theta[LBMK_MAXR];
+    double dlow[LBMK_MAXR][3];                              // falloff: ln(A0/A), b0 - b, theta0 - theta
     double eff[LBMK_MAXR][LBMK_MAXM];
-    // Mixed precision: stored value = population - ref[s][i]; the rest
-    // state of set s at (rho_ref, zeta_ref).  m0 = sum_i ref, m2 = sum_i
-    // ref c_alpha^2 (first and mixed second moments vanish by symmetry).
+    // Mixed precision: stored float value = population - ref[s][i] for the
+    // moving directions of the species and mixture sets (s < M); ref is a
+    // rest state of set s (zero in the rest slot, which is not used).
     float ref[LBMK_MAXS][LBMK_Q];
-    double ref_m0[LBMK_MAXS];
-    double ref_m2[LBMK_MAXS];
 };
 
 struct StepArgs {
     int slot, M, nx, ny, nz, N, bc_x;
     const void *src;     // populations read (pull)
     void *dst;           // populations written
-    double *macro;
+    double *macro;       // double rows, then the storage-type record rows
     void *ghost;
     unsigned *status;
     cudaStream_t stream;

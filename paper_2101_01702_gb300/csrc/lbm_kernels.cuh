@@ -1,22 +1,27 @@
 // Kernels of the fused reactive-mixture lattice Boltzmann step.
 //
 // Included once by each precision translation unit after it defines
-//   LBMK_MIXED 0 : populations stored and collided in double;
-//   LBMK_MIXED 1 : populations stored as float deviations from per-set rest
-//                  states and collided in float; moments are accumulated in
-//                  float and lifted to double with the rest-state moments.
-// In both units the temperature iteration (Eq. (temperature)), the
-// Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
+//   LBMK_MIXED 0 : every population stored and collided in double;
+//   LBMK_MIXED 1 : the moving populations of the species and mixture sets
+//                  stored as float deviations from per-set rest states and
+//                  collided in float; their rest populations and the whole
+//                  energy set in double (see pop_bytes_for).
+// In both units the moments, the temperature iteration (Eq. (temperature)),
+// the Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
 // their equilibrium constants are double precision.
 //
 // One time step is four launches on one stream:
-//   k_ghost  (x-face ghost nodes, Sec. 5a; only for non-periodic x)
-//   k_pre    pull + moments + temperature + Phi and 1/omega - 1/2 (Eq. (Xalpha))
-//   k_grad   G_alpha = (1/omega - 1/2) d_alpha Phi_alpha
-//   k_step   pull + moments + X, grad Y, Stefan-Maxwell, chemistry and the
-//            collisions of Eqs. (finalNumericalEquations), (f), (g)
+//   k_ghost  x-face ghost nodes (Sec. 5a; only for non-periodic x)
+//   k_pre    pull, all moments, Newton temperature, relaxation rates,
+//            Stefan-Maxwell diffusion velocities, production rates, the
+//            local part of the energy-flux correction and the energy
+//            equilibrium moments; writes the per-node record.
+//   k_grad   G_alpha = (1/omega - 1/2) d_alpha Phi_alpha (Eq. (Xalpha))
+//   k_step   pull again, X = -d_alpha G_alpha and sum_a H_a grad Y_a from the
+//            neighbours' records, and the collisions of
+//            Eqs. (finalNumericalEquations), (f), (g), direction by direction
 // One thread owns one lattice node; populations are structure-of-arrays
-// [set][direction][node] so a warp's pulls are coalesced rows.
+// [set][direction][node] so that a warp's pulls are coalesced rows.
 #pragma once
 
 #include <math.h>
@@ -24,18 +29,18 @@
 #include "lbm_internal.h"
 
 #if LBMK_MIXED
-typedef float Store;
 typedef float Real;
 #else
-typedef double Store;
 typedef double Real;
 #endif
 
 #define LBMK_BLOCK 128
 #if LBMK_MIXED
 #define INVWWD(a_, b_) (mc.inv_WWD_f[a_][b_])
+#define RA(a_) (mc.Ra_f[a_])
 #else
 #define INVWWD(a_, b_) (mc.inv_WWD[a_][b_])
+#define RA(a_) (mc.Ra[a_])
 #endif
 
 static __constant__ MechConst c_mech[LBMK_SLOTS];
@@ -43,13 +48,14 @@ static __constant__ MechConst c_mech[LBMK_SLOTS];
 namespace {
 
 // ---------------------------------------------------------------------
-// Lattice helpers.  Direction i = (cx+1) + 3 (cy+1) + 9 (cz+1).
+// Lattice helpers.  Direction i = (cx+1) + 3 (cy+1) + 9 (cz+1); 13 = rest.
 // ---------------------------------------------------------------------
 __host__ __device__ constexpr int CX(int i) { return i % 3 - 1; }
 __host__ __device__ constexpr int CY(int i) { return (i / 3) % 3 - 1; }
 __host__ __device__ constexpr int CZ(int i) { return i / 9 - 1; }
 __host__ __device__ constexpr double W1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
 __host__ __device__ constexpr double WI(int i) { return W1(CX(i)) * W1(CY(i)) * W1(CZ(i)); }
+constexpr int REST = 13;
 
 struct Node {
     int n, x, y, z;
@@ -60,7 +66,7 @@ struct Dir {
     static constexpr int value = I;
 };
 
-// Compile-time loop over directions: f(Dir<0>{}), ..., f(Dir<N-1>{}).
+// Compile-time loop over directions: f(Dir<I>{}), ..., f(Dir<N-1>{}).
 template <int I, int N, class F>
 __device__ __forceinline__ void for_dirs(F &&f)
 {
@@ -72,11 +78,61 @@ __device__ __forceinline__ void for_dirs(F &&f)
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Source coordinates of the pull s(x) = s_post(x - c): index [c+1].
+__device__ __forceinline__ void flag(unsigned *status, unsigned bit) { atomicOr(status, bit); }
+
+// ---------------------------------------------------------------------
+// Population storage (see pop_bytes_for).
+// ---------------------------------------------------------------------
+struct PopView {
+    const void *buf;
+    int N, M;
+#if LBMK_MIXED
+    __device__ const float *mov() const { return static_cast<const float *>(buf); }
+    __device__ const double *rest() const
+    {
+        return reinterpret_cast<const double *>(static_cast<const char *>(buf) + pop_float_bytes(M, N));
+    }
+    __device__ const double *g() const { return rest() + (size_t)M * N; }
+#endif
+};
+
+__device__ __forceinline__ PopView view(const void *buf, const StepArgs &a) { return PopView{buf, a.N, a.M}; }
+
+// Value of species/mixture set s (< M), direction i, at buffer node idx;
+// absolute (the rest state is added back in mixed precision).
+__device__ __forceinline__ Real load_sf(const MechConst &mc, const PopView &v, int s, int i, size_t idx)
+{
+#if LBMK_MIXED
+    if (i == REST) return (Real)v.rest()[(size_t)s * v.N + idx];
+    return __ldg(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx) + mc.ref[s][i];
+#else
+    return __ldg(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
+#endif
+}
+
+// The same in double, keeping the double rest population exact.
+__device__ __forceinline__ double load_sf_d(const MechConst &mc, const PopView &v, int s, int i, size_t idx)
+{
+#if LBMK_MIXED
+    if (i == REST) return v.rest()[(size_t)s * v.N + idx];
+#endif
+    return (double)load_sf(mc, v, s, i, idx);
+}
+
+// Energy-set value, direction i, at buffer node idx (double in both precisions).
+__device__ __forceinline__ double load_g(const PopView &v, int i, size_t idx)
+{
+#if LBMK_MIXED
+    return __ldg(v.g() + (size_t)i * v.N + idx);
+#else
+    return __ldg(static_cast<const double *>(v.buf) + ((size_t)v.M * LBMK_Q + i) * v.N + idx);
+#endif
+}
+
+// Where a pulled population comes from: s(x) = s_post(x - c).
 struct PullIdx {
     int xs[3];    // x - c for c = -1, 0, 1 (may be -1 or nx for ghosts)
-    int row[9];   // nx * (y' + ny z') for (cy, cz)
-    int yz[9];    // y' + ny z'
+    int yz[9];    // y' + ny z' for (cy, cz)
 };
 
 __device__ __forceinline__ void make_pull(PullIdx &p, const Node &nd, const StepArgs &a)
@@ -87,114 +143,139 @@ __device__ __forceinline__ void make_pull(PullIdx &p, const Node &nd, const Step
         p.xs[c + 1] = xs;
     }
     for (int cz = -1; cz <= 1; ++cz)
-        for (int cy = -1; cy <= 1; ++cy) {
-            int ys = wrapi(nd.y - cy, a.ny), zs = wrapi(nd.z - cz, a.nz);
-            int yz = ys + a.ny * zs;
-            p.yz[(cy + 1) + 3 * (cz + 1)] = yz;
-            p.row[(cy + 1) + 3 * (cz + 1)] = a.nx * yz;
-        }
+        for (int cy = -1; cy <= 1; ++cy)
+            p.yz[(cy + 1) + 3 * (cz + 1)] = wrapi(nd.y - cy, a.ny) + a.ny * wrapi(nd.z - cz, a.nz);
 }
 
-// Stored value of set s, direction i pulled to this node.
+// Source of direction i: a buffer node, or (side, plane index) of a ghost.
+struct Src {
+    bool ghost;
+    int side;
+    size_t idx;
+};
+
+__device__ __forceinline__ Src src_of(int i, const PullIdx &p, const StepArgs &a)
+{
+    const int xs = p.xs[CX(i) + 1];
+    const int yz = p.yz[(CY(i) + 1) + 3 * (CZ(i) + 1)];
+    if (a.bc_x == 1 && (xs < 0 || xs >= a.nx)) return Src{true, xs < 0 ? 0 : 1, (size_t)yz};
+    return Src{false, 0, (size_t)xs + (size_t)a.nx * yz};
+}
+
+__device__ __forceinline__ double load_ghost(const StepArgs &a, int side, int s, int i, size_t yz)
+{
+    const size_t plane = (size_t)a.ny * a.nz;
+    return __ldg(static_cast<const double *>(a.ghost) + ((size_t)(side * (a.M + 1) + s) * LBMK_Q + i) * plane + yz);
+}
+
+__device__ __forceinline__ Real pull_sf(const MechConst &mc, const PopView &v, const StepArgs &a, int s, int i,
+                                        const PullIdx &p)
+{
+    const Src sr = src_of(i, p, a);
+    return sr.ghost ? (Real)load_ghost(a, sr.side, s, i, sr.idx) : load_sf(mc, v, s, i, sr.idx);
+}
+
+__device__ __forceinline__ double pull_g(const PopView &v, const StepArgs &a, int i, const PullIdx &p)
+{
+    const Src sr = src_of(i, p, a);
+    return sr.ghost ? load_ghost(a, sr.side, a.M, i, sr.idx) : load_g(v, i, sr.idx);
+}
+
+// Writers of the post-collision state at node n.
+__device__ __forceinline__ void store_sf(const MechConst &mc, void *buf, const StepArgs &a, int s, int i, size_t n,
+                                         double v)
+{
+#if LBMK_MIXED
+    const size_t N = a.N;
+    if (i == REST) {
+        reinterpret_cast<double *>(static_cast<char *>(buf) + pop_float_bytes(a.M, N))[(size_t)s * N + n] = v;
+    } else {
+        static_cast<float *>(buf)[((size_t)s * LBMK_Q + i) * N + n] = (float)v - mc.ref[s][i];
+    }
+#else
+    static_cast<double *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v;
+#endif
+}
+
+__device__ __forceinline__ void store_g(void *buf, const StepArgs &a, int i, size_t n, double v)
+{
+#if LBMK_MIXED
+    const size_t N = a.N;
+    reinterpret_cast<double *>(static_cast<char *>(buf) + pop_float_bytes(a.M, N))[(size_t)a.M * N + (size_t)i * N + n] = v;
+#else
+    static_cast<double *>(buf)[((size_t)a.M * LBMK_Q + i) * a.N + n] = v;
+#endif
+}
+
+// Stencil neighbours x + c (periodic, or clamped for zero-gradient x faces).
+struct StencilIdx {
+    int xs[3];
+    int row[9];
+};
+
+__device__ __forceinline__ void make_stencil(StencilIdx &t, const Node &nd, const StepArgs &a)
+{
+    for (int c = -1; c <= 1; ++c) {
+        int xn = nd.x + c;
+        if (a.bc_x == 0) xn = wrapi(xn, a.nx);
+        else xn = xn < 0 ? 0 : (xn >= a.nx ? a.nx - 1 : xn);
+        t.xs[c + 1] = xn;
+    }
+    for (int cz = -1; cz <= 1; ++cz)
+        for (int cy = -1; cy <= 1; ++cy)
+            t.row[(cy + 1) + 3 * (cz + 1)] = a.nx * (wrapi(nd.y + cy, a.ny) + a.ny * wrapi(nd.z + cz, a.nz));
+}
+
 template <int I>
-__device__ __forceinline__ Store pull_raw(const Store *__restrict__ src, const Store *__restrict__ ghost,
-                                          int s, int S, const PullIdx &p, const StepArgs &a)
+__device__ __forceinline__ size_t nb_of(const StencilIdx &t)
 {
-    const int xs = p.xs[CX(I) + 1];
-    const int k = (CY(I) + 1) + 3 * (CZ(I) + 1);
-    if (CX(I) == 0 || a.bc_x == 0 || (xs >= 0 && xs < a.nx))
-        return __ldg(src + (size_t)(s * LBMK_Q + I) * a.N + xs + p.row[k]);
-    const int side = xs < 0 ? 0 : 1;
-    const int plane = a.ny * a.nz;
-    return __ldg(ghost + ((size_t)(side * S + s) * LBMK_Q + I) * plane + p.yz[k]);
+    return (size_t)t.xs[CX(I) + 1] + t.row[(CY(I) + 1) + 3 * (CZ(I) + 1)];
 }
 
-// Stencil neighbour x + c (periodic, or clamped for zero-gradient x faces).
-__device__ __forceinline__ int stencil_x(int x, int c, const StepArgs &a)
+__device__ __forceinline__ Real *rec(const StepArgs &a)
 {
-    int xn = x + c;
-    if (a.bc_x == 0) return wrapi(xn, a.nx);
-    return xn < 0 ? 0 : (xn >= a.nx ? a.nx - 1 : xn);
-}
-
-__device__ __forceinline__ void flag(const StepArgs &a, unsigned bit)
-{
-    atomicOr(a.status, bit);
+    return reinterpret_cast<Real *>(a.macro + (size_t)macro_double_rows(a.M) * a.N);
 }
 
 // ---------------------------------------------------------------------
 // Thermodynamics (Eqs. (specHa), (Umix), (temperature)).
-// Mixture coefficients: U(T) = sum_k u[k] T^k (k = 0..5), C_v = dU/dT.
 // ---------------------------------------------------------------------
 template <int M>
 __device__ __forceinline__ void mixture_energy_poly(const MechConst &mc, const double *Y, double u[6])
 {
-    if (mc.thermo == 0) {
-        // sum Y_a (U0_a + cv_a (T - T0))
-        double B0 = 0.0, B1 = 0.0;
 #pragma unroll
-        for (int a = 0; a < M; ++a) {
-            B0 = fma(Y[a], mc.U0[a], B0);
-            B1 = fma(Y[a], mc.cv[a], B1);
-        }
-        u[0] = B0 - B1 * mc.T0;
-        u[1] = B1;
-        u[2] = u[3] = u[4] = u[5] = 0.0;
-    } else {
-        // sum Y_a R_a [a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5 + a6 - T]
-        double A[6] = {0, 0, 0, 0, 0, 0}, Rm = 0.0;
+    for (int k = 0; k < 6; ++k) u[k] = 0.0;
 #pragma unroll
-        for (int a = 0; a < M; ++a) {
-            const double yr = Y[a] * mc.Ra[a];
-            Rm += yr;
+    for (int a = 0; a < M; ++a)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) A[k] = fma(yr, mc.poly[a][k], A[k]);
-        }
-        u[0] = A[5];
-        u[1] = A[0] - Rm;
-        u[2] = A[1] * 0.5;
-        u[3] = A[2] * (1.0 / 3.0);
-        u[4] = A[3] * 0.25;
-        u[5] = A[4] * 0.2;
-    }
+        for (int k = 0; k < 6; ++k) u[k] = fma(Y[a], mc.uco[a][k], u[k]);
 }
 
-// Newton iteration on U(T) = e from T_guess; stops when |dT| <= 1e-13 T.
-__device__ __forceinline__ double solve_T(const double u[6], double e, double T, const StepArgs &a)
+__device__ __forceinline__ double poly5(const double u[6], double T)
+{
+    return fma(fma(fma(fma(fma(u[5], T, u[4]), T, u[3]), T, u[2]), T, u[1]), T, u[0]);
+}
+
+// Newton iteration on U(T) = e from T; stops when |dT| <= 1e-13 T.
+__device__ __forceinline__ double solve_T(const double u[6], double e, double T, unsigned *status)
 {
     for (int it = 0; it < 50; ++it) {
-        const double F = fma(fma(fma(fma(fma(u[5], T, u[4]), T, u[3]), T, u[2]), T, u[1]), T, u[0]) - e;
+        const double F = poly5(u, T) - e;
         const double Fp = fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
         const double dT = F / Fp;
         T -= dT;
-        if (!isfinite(T)) { flag(a, LBMK_BIT_NONFINITE); return T; }
+        if (!isfinite(T)) { flag(status, LBMK_BIT_NONFINITE); return T; }
         if (fabs(dT) <= 1e-13 * fabs(T)) return T;
     }
-    flag(a, LBMK_BIT_NEWTON);
+    flag(status, LBMK_BIT_NEWTON);
     return T;
 }
 
 // Species specific enthalpy H_a(T).
 __device__ __forceinline__ double H_spec(const MechConst &mc, int a, double T)
 {
-    if (mc.thermo == 0) return mc.U0[a] + mc.cv[a] * (T - mc.T0) + mc.Ra[a] * T;
-    const double *p = mc.poly[a];
-    // R_a (a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5 + a6)
-    const double h = fma(fma(fma(fma(p[4] * 0.2, T, p[3] * 0.25), T, p[2] * (1.0 / 3.0)), T, p[1] * 0.5), T, p[0]);
-    return mc.Ra[a] * fma(h, T, p[5]);
-}
-
-// Standard Gibbs energy over R_U T of species a.
-__device__ __forceinline__ double gRT_spec(const MechConst &mc, int a, double T, double lnT)
-{
-    if (mc.thermo == 0) {
-        const double h_RT = H_spec(mc, a, T) / (mc.Ra[a] * T);
-        return h_RT - mc.cpR[a] * (lnT - log(mc.T0));
-    }
-    const double *p = mc.poly[a];
-    const double h_RT = fma(fma(fma(fma(p[4] * 0.2, T, p[3] * 0.25), T, p[2] * (1.0 / 3.0)), T, p[1] * 0.5), T, p[0]) + p[5] / T;
-    const double s_R = fma(p[0], lnT, fma(fma(fma(fma(p[4] * 0.25, T, p[3] * (1.0 / 3.0)), T, p[2] * 0.5), T, p[1]), T, p[6]));
-    return h_RT - s_R;
+    const double *h = mc.hco[a];
+    return fma(fma(fma(fma(fma(h[4], T, h[3]), T, h[2]), T, h[1]), T, h[0]), T, h[5]);
 }
 
 __device__ __forceinline__ double nu_prime(const MechConst &mc, double Rm, double T)
@@ -202,97 +283,47 @@ __device__ __forceinline__ double nu_prime(const MechConst &mc, double Rm, doubl
     return mc.visc_model == 0 ? mc.nu / (Rm * T) : mc.nu;
 }
 
-// ---------------------------------------------------------------------
-// Production rates rho_dot_a (Eq. (sumRhoDot)) of the mass-action
-// mechanism.  Species-indexed scratch lives in shared memory, one column
-// per thread, so the reaction tables can index it at run time.
-// ---------------------------------------------------------------------
-template <int M>
-__device__ __forceinline__ void production_rates(const MechConst &mc, const double *rho_a, double T,
-                                                 double *wdot, double *sh)
+// Product-form factor Psi_c(xi, zeta) of Eq. (phis) with s = xi^2 + zeta.
+template <class V>
+__device__ __forceinline__ V psi_c(int c, V xi, V s)
 {
-    double *shc = sh;                         // concentrations
-    double *shw = sh + M * LBMK_BLOCK;        // molar production
-    double *shg = sh + 2 * M * LBMK_BLOCK;    // g_a / (R_U T)
-    const int t = threadIdx.x;
-    const double lnT = log(T), invT = 1.0 / T, lnTr = lnT - mc.log_T_ref;
+    return c == 0 ? (V)1 - s : (V)0.5 * (s + (V)c * xi);
+}
+
+// Energy equilibrium moments (Eqs. (geq1mom), (geq2mom)): q^eq, R^eq -
+// rhoE theta I (xx yy zz xy xz yz) and a third of its trace.
+__device__ __forceinline__ void energy_moments(double rho, const double *u, double P, double hk, double rhoE,
+                                               double qeq[3], double Rt[6], double &tr3)
+{
+    const double hP = hk * rho + P;
 #pragma unroll
-    for (int a = 0; a < M; ++a) {
-        shc[a * LBMK_BLOCK + t] = rho_a[a] * mc.invW[a];
-        shw[a * LBMK_BLOCK + t] = 0.0;
-        shg[a * LBMK_BLOCK + t] = gRT_spec(mc, a, T, lnT);
+    for (int d = 0; d < 3; ++d) {
+        qeq[d] = hk * rho * u[d];
+        Rt[d] = hk * P + hP * u[d] * u[d] - rhoE / 3.0;
     }
-    const double lnc0 = mc.log_P0_over_r - lnT;     // ln(P0 / (r T))
-    for (int k = 0; k < mc.R; ++k) {
-        const double lk = mc.log_A[k] + mc.b[k] * lnTr - mc.theta[k] * invT;
-        double kf = exp(lk);
-        double cM = 0.0;
-        const int type = mc.rtype[k];
-        if (type != 0) {
-#pragma unroll
-            for (int a = 0; a < M; ++a) cM = fma(mc.eff[k][a], shc[a * LBMK_BLOCK + t], cM);
-        }
-        if (type == 2) {
-            const double k0 = exp(mc.low[k][0] + mc.low[k][1] * lnTr - mc.low[k][2] * invT);
-            const double Pr = k0 * cM / kf;
-            kf = kf * Pr / (1.0 + Pr);
-        }
-        double qf = kf;
-        for (int j = 0; j < mc.nreac[k]; ++j) qf *= shc[mc.reac[k][j] * LBMK_BLOCK + t];
-        double q = qf;
-        if (mc.rev[k]) {
-            double dG = 0.0;
-            for (int j = 0; j < mc.ndnu[k]; ++j) dG += mc.dnu_v[k][j] * shg[mc.dnu_sp[k][j] * LBMK_BLOCK + t];
-            // k_r = k_f / K_c, K_c = exp(-dG) (P0/(r T))^dn
-            double qr = kf * exp(dG - mc.dn[k] * lnc0);
-            for (int j = 0; j < mc.nprod[k]; ++j) qr *= shc[mc.prod[k][j] * LBMK_BLOCK + t];
-            q -= qr;
-        }
-        if (type == 1) q *= cM;
-        for (int j = 0; j < mc.nreac[k]; ++j) shw[mc.reac[k][j] * LBMK_BLOCK + t] -= q;
-        for (int j = 0; j < mc.nprod[k]; ++j) shw[mc.prod[k][j] * LBMK_BLOCK + t] += q;
-    }
-#pragma unroll
-    for (int a = 0; a < M; ++a) wdot[a] = mc.W[a] * shw[a * LBMK_BLOCK + t];
+    Rt[3] = hP * u[0] * u[1];
+    Rt[4] = hP * u[0] * u[2];
+    Rt[5] = hP * u[1] * u[2];
+    tr3 = (Rt[0] + Rt[1] + Rt[2]) * (1.0 / 3.0);
 }
 
-// ---------------------------------------------------------------------
-// Product-form factors (Eq. (phis)): P[c+1] = Psi_c(xi, zeta).
-// ---------------------------------------------------------------------
-__device__ __forceinline__ void psi3(Real xi, Real zeta, Real P[3])
+// Grad population of direction i (Eqs. (gieq), (giqeq)) for given moments.
+__device__ __forceinline__ double grad_dir(int i, double rhoE, const double q[3], const double Rt[6], double tr3)
 {
-    const Real s = xi * xi + zeta;
-    P[0] = (Real)0.5 * (s - xi);
-    P[1] = (Real)1 - s;
-    P[2] = (Real)0.5 * (s + xi);
+    const int cx = CX(i), cy = CY(i), cz = CZ(i);
+    double qc = 0.0, rcc = 0.0;
+    if (cx) { qc += cx * q[0]; rcc += Rt[0]; }
+    if (cy) { qc += cy * q[1]; rcc += Rt[1]; }
+    if (cz) { qc += cz * q[2]; rcc += Rt[2]; }
+    if (cx && cy) rcc += 2.0 * (cx * cy) * Rt[3];
+    if (cx && cz) rcc += 2.0 * (cx * cz) * Rt[4];
+    if (cy && cz) rcc += 2.0 * (cy * cz) * Rt[5];
+    return WI(i) * (rhoE + 3.0 * qc + 4.5 * (rcc - tr3));
 }
 
-// Store a post-collision value (deviation from the rest state in mixed mode).
-template <int I>
-__device__ __forceinline__ void put(Store *__restrict__ dst, const MechConst &mc, int s, size_t N, int n, Real v)
-{
-#if LBMK_MIXED
-    dst[(size_t)(s * LBMK_Q + I) * N + n] = v - mc.ref[s][I];
-#else
-    dst[(size_t)(s * LBMK_Q + I) * N + n] = v;
-#endif
-}
-
-template <int I>
-__device__ __forceinline__ Real absval(const MechConst &mc, int s, Store v)
-{
-#if LBMK_MIXED
-    return v + mc.ref[s][I];
-#else
-    return v;
-#endif
-}
-
-// Equilibrium populations of every set at (rho_a, u, T); written as the
-// stored representation to out[(s*27+i)*stride + off].
-template <int M>
-__device__ void write_equilibria(const MechConst &mc, const double *rho_a, const double *u, double T,
-                                 Store *out, size_t stride, size_t off)
+// Equilibrium of every set at (rho_a, u, T), in double, handed to put(s, i, v).
+template <int M, class Put>
+__device__ void equilibria(const MechConst &mc, const double *rho_a, const double *u, double T, Put &&put)
 {
     double rho = 0.0;
 #pragma unroll
@@ -304,50 +335,28 @@ __device__ void write_equilibria(const MechConst &mc, const double *rho_a, const
     const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        const Real zeta = (Real)((s < M - 1 ? mc.Ra[s] : Rm) * T);
-        const Real r = (Real)(s < M - 1 ? rho_a[s] : rho);
-        Real Px[3], Py[3], Pz[3];
-        psi3((Real)u[0], zeta, Px);
-        psi3((Real)u[1], zeta, Py);
-        psi3((Real)u[2], zeta, Pz);
+        const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T;
+        const double r = s < M - 1 ? rho_a[s] : rho;
+        double P3[3][3];
 #pragma unroll
-        for (int i = 0; i < LBMK_Q; ++i) {
-            Real v = r * Px[CX(i) + 1] * Py[CY(i) + 1] * Pz[CZ(i) + 1];
-#if LBMK_MIXED
-            v -= mc.ref[s][i];
-#endif
-            out[(size_t)(s * LBMK_Q + i) * stride + off] = v;
-        }
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int c = -1; c <= 1; ++c) P3[d][c + 1] = psi_c(c, u[d], u[d] * u[d] + zeta);
+#pragma unroll
+        for (int i = 0; i < LBMK_Q; ++i) put(s, i, r * P3[0][CX(i) + 1] * P3[1][CY(i) + 1] * P3[2][CZ(i) + 1]);
     }
     double eu[6];
     mixture_energy_poly<M>(mc, Y, eu);
-    const double U = fma(fma(fma(fma(fma(eu[5], T, eu[4]), T, eu[3]), T, eu[2]), T, eu[1]), T, eu[0]);
+    const double U = poly5(eu, T);
     double H = 0.0;
 #pragma unroll
     for (int a = 0; a < M; ++a) H = fma(Y[a], H_spec(mc, a, T), H);
     const double rhoE = rho * (U + 0.5 * usq);
     const double P = rho * Rm * T;
-    const double hk = H + 0.5 * usq;
-    double R[3][3];
+    double q[3], Rt[6], tr3;
+    energy_moments(rho, u, P, H + 0.5 * usq, rhoE, q, Rt, tr3);
 #pragma unroll
-    for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be)
-            R[al][be] = hk * ((al == be ? P : 0.0) + rho * u[al] * u[be]) + P * u[al] * u[be];
-    const double tr3 = (R[0][0] + R[1][1] + R[2][2] - rhoE) * (1.0 / 3.0);   // tr(R - rhoE theta I)/3
-#pragma unroll
-    for (int i = 0; i < LBMK_Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
-        const double qc = hk * rho * (u[0] * cx + u[1] * cy + u[2] * cz);
-        const double rcc = (R[0][0] - rhoE / 3.0) * (cx * cx) + (R[1][1] - rhoE / 3.0) * (cy * cy) +
-                           (R[2][2] - rhoE / 3.0) * (cz * cz) +
-                           2.0 * (R[0][1] * (cx * cy) + R[0][2] * (cx * cz) + R[1][2] * (cy * cz));
-        Real v = (Real)(WI(i) * (rhoE + 3.0 * qc + 4.5 * (rcc - tr3)));
-#if LBMK_MIXED
-        v -= mc.ref[M][i];
-#endif
-        out[(size_t)(M * LBMK_Q + i) * stride + off] = v;
-    }
+    for (int i = 0; i < LBMK_Q; ++i) put(M, i, grad_dir(i, rhoE, q, Rt, tr3));
 }
 
 __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
@@ -359,6 +368,71 @@ __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
     nd.y = r % a.ny;
     nd.z = r / a.ny;
     return true;
+}
+
+// Moments of the pulled populations.  Species a < M-1 give rho_a and j_a;
+// f gives rho, j and (WITH_P) the pressure tensor; g gives rho E and q.
+struct Sums {
+    double rho, j[3], P[6], rhoE, q[3];   // P: xx, yy, zz, xy, xz, yz
+};
+
+template <int M, bool WITH_P>
+__device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs &a, const PullIdx &p, int n,
+                                             double *rho_a, double (*ja)[3], Sums &sm)
+{
+    const PopView v = view(a.src, a);
+#pragma unroll
+    for (int s = 0; s < M - 1; ++s) {
+        Real a0 = 0, ax = 0, ay = 0, az = 0;
+        for_dirs<0, LBMK_Q>([&](auto d) {
+            constexpr int I = decltype(d)::value;
+            if (LBMK_MIXED && I == REST) return;
+            const Real f = pull_sf(mc, v, a, s, I, p);
+            a0 += f;
+            if (CX(I)) ax += CX(I) * f;
+            if (CY(I)) ay += CY(I) * f;
+            if (CZ(I)) az += CZ(I) * f;
+        });
+        rho_a[s] = (double)a0;
+#if LBMK_MIXED
+        rho_a[s] += v.rest()[(size_t)s * a.N + n];
+#endif
+        ja[s][0] = ax;
+        ja[s][1] = ay;
+        ja[s][2] = az;
+    }
+    Real a0 = 0, ax = 0, ay = 0, az = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+    double g0 = 0, qx = 0, qy = 0, qz = 0;
+    for_dirs<0, LBMK_Q>([&](auto d) {
+        constexpr int I = decltype(d)::value;
+        const double g = pull_g(v, a, I, p);
+        g0 += g;
+        if (CX(I)) qx += CX(I) * g;
+        if (CY(I)) qy += CY(I) * g;
+        if (CZ(I)) qz += CZ(I) * g;
+        if (LBMK_MIXED && I == REST) return;
+        const Real f = pull_sf(mc, v, a, M - 1, I, p);
+        a0 += f;
+        if (CX(I)) ax += CX(I) * f;
+        if (CY(I)) ay += CY(I) * f;
+        if (CZ(I)) az += CZ(I) * f;
+        if constexpr (WITH_P) {
+            if (CX(I)) pxx += f;
+            if (CY(I)) pyy += f;
+            if (CZ(I)) pzz += f;
+            if (CX(I) && CY(I)) pxy += (CX(I) * CY(I)) * f;
+            if (CX(I) && CZ(I)) pxz += (CX(I) * CZ(I)) * f;
+            if (CY(I) && CZ(I)) pyz += (CY(I) * CZ(I)) * f;
+        }
+    });
+    sm.rho = (double)a0;
+    sm.rhoE = g0;
+    sm.j[0] = ax; sm.j[1] = ay; sm.j[2] = az;
+    sm.q[0] = qx; sm.q[1] = qy; sm.q[2] = qz;
+    sm.P[0] = pxx; sm.P[1] = pyy; sm.P[2] = pzz; sm.P[3] = pxy; sm.P[4] = pxz; sm.P[5] = pyz;
+#if LBMK_MIXED
+    sm.rho += v.rest()[(size_t)(M - 1) * a.N + n];
+#endif
 }
 
 // ---------------------------------------------------------------------
@@ -383,12 +457,16 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_init(StepArgs a, const double *X
     double u[3] = {0.0, 0.0, 0.0};
     if (uf)
         for (int d = 0; d < 3; ++d) u[d] = uf[(size_t)d * a.N + n];
-    write_equilibria<M>(mc, rho_a, u, T, (Store *)a.dst, a.N, n);
-    a.macro[(size_t)MAC_T * a.N + n] = T;
+    equilibria<M>(mc, rho_a, u, T, [&](int s, int i, double v) {
+        if (s < M) store_sf(mc, a.dst, a, s, i, n, v);
+        else store_g(a.dst, a, i, n, v);
+    });
+    a.macro[(size_t)DR_T * a.N + n] = T;
 }
 
 // ---------------------------------------------------------------------
-// Ghost nodes beyond the x faces (Sec. 5a).
+// Ghost nodes beyond the x faces (Sec. 5a): equilibria at the
+// post-collision moments of the adjacent boundary node, u = 0 on the left.
 // ---------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
@@ -398,39 +476,23 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * plane) return;
     const int side = t / plane, yz = t % plane;
-    const int n = (side ? a.nx - 1 : 0) + a.nx * yz;
-    const Store *src = (const Store *)a.src;
+    const size_t n = (size_t)(side ? a.nx - 1 : 0) + (size_t)a.nx * yz;
+    const PopView v = view(a.src, a);
     double rho_a[M], rho = 0.0, j[3] = {0, 0, 0}, rhoE = 0.0;
     double rest = 0.0;
-#pragma unroll
     for (int s = 0; s < M - 1; ++s) {
-        Real acc = 0;
-#pragma unroll
-        for (int i = 0; i < LBMK_Q; ++i) acc += src[(size_t)(s * LBMK_Q + i) * a.N + n];
-        rho_a[s] = (double)acc;
-#if LBMK_MIXED
-        rho_a[s] += mc.ref_m0[s];
-#endif
-        rest += rho_a[s];
+        double acc = 0.0;
+        for (int i = 0; i < LBMK_Q; ++i) acc += load_sf_d(mc, v, s, i, n);
+        rho_a[s] = acc;
+        rest += acc;
     }
-    {
-        Real a0 = 0, ax = 0, ay = 0, az = 0, ag = 0;
-#pragma unroll
-        for (int i = 0; i < LBMK_Q; ++i) {
-            const Real f = src[(size_t)((M - 1) * LBMK_Q + i) * a.N + n];
-            a0 += f;
-            if (CX(i)) ax += CX(i) * f;
-            if (CY(i)) ay += CY(i) * f;
-            if (CZ(i)) az += CZ(i) * f;
-            ag += src[(size_t)(M * LBMK_Q + i) * a.N + n];
-        }
-        rho = (double)a0;
-        rhoE = (double)ag;
-#if LBMK_MIXED
-        rho += mc.ref_m0[M - 1];
-        rhoE += mc.ref_m0[M];
-#endif
-        j[0] = ax; j[1] = ay; j[2] = az;
+    for (int i = 0; i < LBMK_Q; ++i) {
+        const double f = load_sf_d(mc, v, M - 1, i, n);
+        rho += f;
+        j[0] += CX(i) * f;
+        j[1] += CY(i) * f;
+        j[2] += CZ(i) * f;
+        rhoE += load_g(v, i, n);
     }
     rho_a[M - 1] = rho - rest;
     double Y[M];
@@ -440,263 +502,130 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
     const double e = rhoE / rho - 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     double eu[6];
     mixture_energy_poly<M>(mc, Y, eu);
-    const double T = solve_T(eu, e, a.macro[(size_t)MAC_T * a.N + n], a);
+    const double T = solve_T(eu, e, a.macro[(size_t)DR_T * a.N + n], a.status);
     if (side == 0) u[0] = u[1] = u[2] = 0.0;
-    write_equilibria<M>(mc, rho_a, u, T, (Store *)a.ghost + (size_t)side * (M + 1) * LBMK_Q * plane, plane, yz);
+    double *gh = static_cast<double *>(a.ghost) + (size_t)side * (M + 1) * LBMK_Q * plane;
+    equilibria<M>(mc, rho_a, u, T, [&](int s, int i, double val) { gh[((size_t)s * LBMK_Q + i) * plane + yz] = val; });
 }
 
 // ---------------------------------------------------------------------
-// Pass 1: pull, moments, temperature, Phi, 1/omega - 1/2.  With OUT the
-// requested fields go to `out` instead of the macroscopic record.
+// Moments for lbm_moments: the fields of the state in src (no record).
 // ---------------------------------------------------------------------
-template <int M, bool OUT>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a, unsigned mask, double *out)
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mask, double *out)
 {
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
     PullIdx p;
     make_pull(p, nd, a);
-    const Store *src = (const Store *)a.src;
-    const Store *gh = (const Store *)a.ghost;
-    constexpr int S = M + 1;
     double rho_a[M], ja[M][3];
+    Sums sm;
+    pull_moments<M, false>(mc, a, p, nd.n, rho_a, ja, sm);
+    const double rho = sm.rho;
     double rest = 0.0;
 #pragma unroll
-    for (int s = 0; s < M - 1; ++s) {
-        Real a0 = 0, ax = 0, ay = 0, az = 0;
-        for_dirs<0, LBMK_Q>([&](auto d) {
-            constexpr int I = decltype(d)::value;
-            const Real f = pull_raw<I>(src, gh, s, S, p, a);
-            a0 += f;
-            if (CX(I)) ax += CX(I) * f;
-            if (CY(I)) ay += CY(I) * f;
-            if (CZ(I)) az += CZ(I) * f;
-        });
-        rho_a[s] = (double)a0;
-#if LBMK_MIXED
-        rho_a[s] += mc.ref_m0[s];
-#endif
-        ja[s][0] = ax; ja[s][1] = ay; ja[s][2] = az;
-        rest += rho_a[s];
-    }
-    double rho, j[3], rhoE;
-    {
-        Real a0 = 0, ax = 0, ay = 0, az = 0, ag = 0;
-        for_dirs<0, LBMK_Q>([&](auto d) {
-            constexpr int I = decltype(d)::value;
-            const Real f = pull_raw<I>(src, gh, M - 1, S, p, a);
-            const Real g = pull_raw<I>(src, gh, M, S, p, a);
-            a0 += f;
-            ag += g;
-            if (CX(I)) ax += CX(I) * f;
-            if (CY(I)) ay += CY(I) * f;
-            if (CZ(I)) az += CZ(I) * f;
-        });
-        rho = (double)a0;
-        rhoE = (double)ag;
-#if LBMK_MIXED
-        rho += mc.ref_m0[M - 1];
-        rhoE += mc.ref_m0[M];
-#endif
-        j[0] = ax; j[1] = ay; j[2] = az;
-    }
+    for (int s = 0; s < M - 1; ++s) rest += rho_a[s];
     rho_a[M - 1] = rho - rest;
     double Y[M], inv_m = 0.0;
-    bool neg = false;
 #pragma unroll
-    for (int s = 0; s < M; ++s) {
-        Y[s] = rho_a[s] / rho;
-        inv_m += Y[s] * mc.invW[s];
-        neg |= rho_a[s] < -1e-10 * rho;      // below rounding noise of trace species
-    }
-    if (!(rho > 0.0) || !isfinite(rhoE)) flag(a, LBMK_BIT_NONFINITE);
-    if (neg) flag(a, LBMK_BIT_NEGATIVE);
-    const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+    for (int s = 0; s < M; ++s) { Y[s] = rho_a[s] / rho; inv_m += Y[s] * mc.invW[s]; }
+    const double u[3] = {sm.j[0] / rho, sm.j[1] / rho, sm.j[2] / rho};
     const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     double eu[6];
     mixture_energy_poly<M>(mc, Y, eu);
     const int n = nd.n;
     const size_t N = a.N;
-    const double T = solve_T(eu, rhoE / rho - 0.5 * usq, a.macro[MAC_T * N + n], a);
+    const double T = solve_T(eu, sm.rhoE / rho - 0.5 * usq, a.macro[DR_T * N + n], a.status);
     const double Rm = mc.r_lat * inv_m;
-    if (!OUT) {
-        a.macro[MAC_T * N + n] = T;
-        a.macro[MAC_NUP * N + n] = nu_prime(mc, Rm, T);
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-            a.macro[(MAC_PHI + d) * N + n] = rho * u[d] * (1.0 - 3.0 * Rm * T) - rho * u[d] * u[d] * u[d];
-#pragma unroll
-        for (int s = 0; s < M; ++s) a.macro[(MAC_Y + s) * N + n] = Y[s];
-    } else {
-        size_t row = 0;
-        if (mask & 1u) { for (int s = 0; s < M; ++s) out[(row + s) * N + n] = rho_a[s]; row += M; }
-        if (mask & 2u) { for (int d = 0; d < 3; ++d) out[(row + d) * N + n] = j[d]; row += 3; }
-        if (mask & 4u) { out[row * N + n] = rhoE; row += 1; }
-        if (mask & 8u) { out[row * N + n] = T; row += 1; }
-        if (mask & 16u) { out[row * N + n] = rho * Rm * T; row += 1; }
-        if (mask & 32u) { for (int s = 0; s < M; ++s) out[(row + s) * N + n] = Y[s]; row += M; }
-        if (mask & 64u) {
-            double jM[3] = {j[0], j[1], j[2]};
-            for (int s = 0; s < M - 1; ++s)
-                for (int d = 0; d < 3; ++d) { out[(row + 3 * s + d) * N + n] = ja[s][d]; jM[d] -= ja[s][d]; }
-            for (int d = 0; d < 3; ++d) out[(row + 3 * (M - 1) + d) * N + n] = jM[d];
-        }
+    size_t row = 0;
+    if (mask & 1u) { for (int s = 0; s < M; ++s) out[(row + s) * N + n] = rho_a[s]; row += M; }
+    if (mask & 2u) { for (int d = 0; d < 3; ++d) out[(row + d) * N + n] = sm.j[d]; row += 3; }
+    if (mask & 4u) { out[row * N + n] = sm.rhoE; row += 1; }
+    if (mask & 8u) { out[row * N + n] = T; row += 1; }
+    if (mask & 16u) { out[row * N + n] = rho * Rm * T; row += 1; }
+    if (mask & 32u) { for (int s = 0; s < M; ++s) out[(row + s) * N + n] = Y[s]; row += M; }
+    if (mask & 64u) {
+        double jM[3] = {sm.j[0], sm.j[1], sm.j[2]};
+        for (int s = 0; s < M - 1; ++s)
+            for (int d = 0; d < 3; ++d) { out[(row + 3 * s + d) * N + n] = ja[s][d]; jM[d] -= ja[s][d]; }
+        for (int d = 0; d < 3; ++d) out[(row + 3 * (M - 1) + d) * N + n] = jM[d];
     }
 }
 
 // ---------------------------------------------------------------------
-// Pass 2: G_alpha = (1/omega - 1/2) d_alpha Phi_alpha with the isotropic
-// gradient d_alpha phi = (1/theta) sum_i w_i c_ia phi(x + c_i).
-// ---------------------------------------------------------------------
-__global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
-{
-    Node nd;
-    if (!node_of(nd, a)) return;
-    const size_t N = a.N;
-    const double *Phi = a.macro + MAC_PHI * N;
-    double d[3] = {0.0, 0.0, 0.0};
-    int xs[3], rows[9];
-    for (int c = -1; c <= 1; ++c) xs[c + 1] = stencil_x(nd.x, c, a);
-    for (int cz = -1; cz <= 1; ++cz)
-        for (int cy = -1; cy <= 1; ++cy)
-            rows[(cy + 1) + 3 * (cz + 1)] = a.nx * (wrapi(nd.y + cy, a.ny) + a.ny * wrapi(nd.z + cz, a.nz));
-#pragma unroll
-    for (int i = 0; i < LBMK_Q; ++i) {
-        const size_t nb = xs[CX(i) + 1] + rows[(CY(i) + 1) + 3 * (CZ(i) + 1)];
-        if (CX(i)) d[0] += (WI(i) * CX(i)) * Phi[nb];
-        if (CY(i)) d[1] += (WI(i) * CY(i)) * Phi[N + nb];
-        if (CZ(i)) d[2] += (WI(i) * CZ(i)) * Phi[2 * N + nb];
-    }
-    const double nup = a.macro[MAC_NUP * N + nd.n];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a.macro[(MAC_G + k) * N + nd.n] = nup * 3.0 * d[k];
-}
-
-// ---------------------------------------------------------------------
-// Pass 3: the fused collision.
+// Pass 1: pull, moments, temperature, relaxation, Stefan-Maxwell solve,
+// chemistry; writes the per-node record.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
+__global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
 {
-    __shared__ double sh_chem[3 * M * LBMK_BLOCK];
+    __shared__ double sh_act[M * LBMK_BLOCK];   // c_a exp(g_a / R_U T)
+    __shared__ double sh_g[M * LBMK_BLOCK];     // g_a / R_U T
+    __shared__ double sh_w[M * LBMK_BLOCK];     // molar production
     const MechConst &mc = c_mech[a.slot];
+    const int t = threadIdx.x;
     Node nd;
-    const bool live = node_of(nd, a);
-    if (!live) return;
-    const int n = nd.n;
-    const size_t N = a.N;
-    const double T = a.macro[MAC_T * N + n];
-
-    // species enthalpies at T (Eq. (specHa))
-    double Ha[M];
-#pragma unroll
-    for (int s = 0; s < M; ++s) Ha[s] = H_spec(mc, s, T);
-
-    // X = -d_alpha G_alpha (Eq. (Xalpha)) and sum_a H_a grad Y_a (Eq. (corrFourier))
-    double X[3] = {0, 0, 0}, HgY[3] = {0, 0, 0};
-    {
-        int xs[3], rows[9];
-        for (int c = -1; c <= 1; ++c) xs[c + 1] = stencil_x(nd.x, c, a);
-        for (int cz = -1; cz <= 1; ++cz)
-            for (int cy = -1; cy <= 1; ++cy)
-                rows[(cy + 1) + 3 * (cz + 1)] = a.nx * (wrapi(nd.y + cy, a.ny) + a.ny * wrapi(nd.z + cz, a.nz));
-        const double *G = a.macro + MAC_G * N;
-        const double *Yf = a.macro + MAC_Y * N;
-#pragma unroll
-        for (int i = 0; i < LBMK_Q; ++i) {
-            if (i == 13) continue;
-            const size_t nb = xs[CX(i) + 1] + rows[(CY(i) + 1) + 3 * (CZ(i) + 1)];
-            double hy = 0.0;
-#pragma unroll
-            for (int s = 0; s < M; ++s) hy = fma(Ha[s], Yf[s * N + nb], hy);
-            if (CX(i)) { X[0] += (WI(i) * CX(i)) * G[nb]; HgY[0] += (WI(i) * CX(i)) * hy; }
-            if (CY(i)) { X[1] += (WI(i) * CY(i)) * G[N + nb]; HgY[1] += (WI(i) * CY(i)) * hy; }
-            if (CZ(i)) { X[2] += (WI(i) * CZ(i)) * G[2 * N + nb]; HgY[2] += (WI(i) * CZ(i)) * hy; }
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { X[k] *= -3.0; HgY[k] *= 3.0; }
-    }
-
+    if (!node_of(nd, a)) return;
     PullIdx p;
     make_pull(p, nd, a);
-    const Store *src = (const Store *)a.src;
-    const Store *gh = (const Store *)a.ghost;
-    Store *dst = (Store *)a.dst;
-    constexpr int S = M + 1;
-
-    // sweep 1: moments of the pulled populations
     double rho_a[M], ja[M][3];
+    Sums sm;
+    pull_moments<M, true>(mc, a, p, nd.n, rho_a, ja, sm);
+
+    // composition and velocity (Eq. (strongest) for the slaved species)
+    const double rho = sm.rho, ir = 1.0 / rho;
     double rest = 0.0;
 #pragma unroll
-    for (int s = 0; s < M - 1; ++s) {
-        Real a0 = 0, ax = 0, ay = 0, az = 0;
-        for_dirs<0, LBMK_Q>([&](auto d) {
-            constexpr int I = decltype(d)::value;
-            const Real f = pull_raw<I>(src, gh, s, S, p, a);
-            a0 += f;
-            if (CX(I)) ax += CX(I) * f;
-            if (CY(I)) ay += CY(I) * f;
-            if (CZ(I)) az += CZ(I) * f;
-        });
-        rho_a[s] = (double)a0;
-#if LBMK_MIXED
-        rho_a[s] += mc.ref_m0[s];
-#endif
-        ja[s][0] = ax; ja[s][1] = ay; ja[s][2] = az;
-        rest += rho_a[s];
-    }
-    double rho, j[3], rhoE, q[3], Pt[6];   // Pt: xx, yy, zz, xy, xz, yz
-    {
-        Real a0 = 0, ax = 0, ay = 0, az = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-        Real g0 = 0, qx = 0, qy = 0, qz = 0;
-        for_dirs<0, LBMK_Q>([&](auto d) {
-            constexpr int I = decltype(d)::value;
-            const Real f = pull_raw<I>(src, gh, M - 1, S, p, a);
-            const Real g = pull_raw<I>(src, gh, M, S, p, a);
-            a0 += f;
-            g0 += g;
-            if (CX(I)) { ax += CX(I) * f; pxx += f; qx += CX(I) * g; }
-            if (CY(I)) { ay += CY(I) * f; pyy += f; qy += CY(I) * g; }
-            if (CZ(I)) { az += CZ(I) * f; pzz += f; qz += CZ(I) * g; }
-            if (CX(I) && CY(I)) pxy += (CX(I) * CY(I)) * f;
-            if (CX(I) && CZ(I)) pxz += (CX(I) * CZ(I)) * f;
-            if (CY(I) && CZ(I)) pyz += (CY(I) * CZ(I)) * f;
-        });
-        rho = (double)a0;
-        rhoE = (double)g0;
-        Pt[0] = pxx; Pt[1] = pyy; Pt[2] = pzz;
-#if LBMK_MIXED
-        rho += mc.ref_m0[M - 1];
-        rhoE += mc.ref_m0[M];
-        Pt[0] += mc.ref_m2[M - 1]; Pt[1] += mc.ref_m2[M - 1]; Pt[2] += mc.ref_m2[M - 1];
-#endif
-        Pt[3] = pxy; Pt[4] = pxz; Pt[5] = pyz;
-        j[0] = ax; j[1] = ay; j[2] = az;
-        q[0] = qx; q[1] = qy; q[2] = qz;
-    }
+    for (int s = 0; s < M - 1; ++s) rest += rho_a[s];
     rho_a[M - 1] = rho - rest;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double js = j[d];
+        double js = sm.j[d];
 #pragma unroll
         for (int s = 0; s < M - 1; ++s) js -= ja[s][d];
         ja[M - 1][d] = js;
     }
     double Y[M], inv_m = 0.0;
+    bool neg = false;
 #pragma unroll
-    for (int s = 0; s < M; ++s) { Y[s] = rho_a[s] / rho; inv_m += Y[s] * mc.invW[s]; }
-    const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+    for (int s = 0; s < M; ++s) {
+        Y[s] = rho_a[s] * ir;
+        inv_m = fma(Y[s], mc.invW[s], inv_m);
+        neg |= rho_a[s] < -1e-10 * rho;      // below rounding noise of trace species
+    }
+    if (!(rho > 0.0) || !isfinite(sm.rhoE)) flag(a.status, LBMK_BIT_NONFINITE);
+    if (neg) flag(a.status, LBMK_BIT_NEGATIVE);
+    const double u[3] = {sm.j[0] * ir, sm.j[1] * ir, sm.j[2] * ir};
     const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const double m = 1.0 / inv_m;
+
+    // temperature, Eq. (temperature)
+    const int n = nd.n;
+    const size_t N = a.N;
+    double T;
+    {
+        double eu[6];
+        mixture_energy_poly<M>(mc, Y, eu);
+        T = solve_T(eu, sm.rhoE * ir - 0.5 * usq, a.macro[DR_T * N + n], a.status);
+    }
     const double Rm = mc.r_lat * inv_m;
     const double P = rho * Rm * T;
     const double nup = nu_prime(mc, Rm, T);
     const double omega = 1.0 / (0.5 + nup);
     const double omega1 = 1.0 / (0.5 + nup / mc.Pr);
+    const double invT = 1.0 / T, lnT = log(T);
 
-    // Eq. (tauab): 1/tau_ab = kappa / (W_a W_b D_ab), kappa = m R_U T
-    const double kappa = m * mc.r_lat * T;
+    // enthalpies, Eq. (specHa)
+    double Ha[M], H = 0.0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        Ha[s] = H_spec(mc, s, T);
+        H = fma(Y[s], Ha[s], H);
+    }
+
+    // Eq. (tauab): 1/tau_ab = kappa / (W_a W_b D_ab), kappa = m R_U T;
+    // 1/tau_a = sum_b Y_b / tau_ab.
+    const double kappa = mc.r_lat * T / inv_m;
     double ita[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
@@ -707,162 +636,388 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
         ita[s] = kappa * acc;
     }
 
-    // Eq. (transform1): Gaussian elimination (the matrix is strictly
-    // diagonally dominant, so no pivoting), three right-hand sides.
+    // Eq. (transform1), multiplied by Y_a so that the matrix is symmetric:
+    //   B_aa = Y_a (1 + 1/(2 tau_a)),  B_ab = -(1/2) Y_a Y_b / tau_ab,
+    //   rhs_a = Y_a (u_a - u) = j_a / rho - Y_a u.
+    // B is symmetric positive definite; L D L^T without pivoting, L unit
+    // lower triangular (stored below the diagonal of Ln).
     double du[M][3];
     {
-        double A[M][M], rhs[M][3];
+        double Ln[M][M], D[M], Dinv[M];
 #pragma unroll
-        for (int s = 0; s < M; ++s) {
+        for (int i = 0; i < M; ++i) {
+            const double hy = -0.5 * kappa * Y[i];
 #pragma unroll
-            for (int b = 0; b < M; ++b)
-                A[s][b] = (s == b) ? 1.0 + 0.5 * ita[s] : -0.5 * kappa * mc.inv_WWD[s][b] * Y[b];
-            const double ir = 1.0 / rho_a[s];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) rhs[s][d] = ja[s][d] * ir - u[d];
+            for (int k = 0; k < i; ++k) Ln[i][k] = hy * mc.inv_WWD[i][k] * Y[k];
+            Ln[i][i] = Y[i] * fma(0.5, ita[i], 1.0);
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            if (A[k][k] == 0.0) flag(a, LBMK_BIT_PIVOT);
-            const double ip = 1.0 / A[k][k];
+            double tk[M];
 #pragma unroll
-            for (int r = k + 1; r < M; ++r) {
-                const double l = A[r][k] * ip;
+            for (int j = 0; j < k; ++j) tk[j] = D[j] * Ln[k][j];
 #pragma unroll
-                for (int c = k + 1; c < M; ++c) A[r][c] = fma(-l, A[k][c], A[r][c]);
+            for (int i = k; i < M; ++i) {
+                double sacc = Ln[i][k];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) rhs[r][d] = fma(-l, rhs[k][d], rhs[r][d]);
+                for (int j = 0; j < k; ++j) sacc = fma(-Ln[i][j], tk[j], sacc);
+                Ln[i][k] = sacc;
             }
-        }
+            D[k] = Ln[k][k];
+            if (!(D[k] > 0.0)) flag(a.status, LBMK_BIT_PIVOT);
+            Dinv[k] = 1.0 / D[k];
 #pragma unroll
-        for (int r = M - 1; r >= 0; --r) {
-            const double ip = 1.0 / A[r][r];
+            for (int i = k + 1; i < M; ++i) Ln[i][k] *= Dinv[k];
+        }
+        // L z = rhs, z /= D, L^T x = z
+#pragma unroll
+        for (int i = 0; i < M; ++i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double acc = rhs[r][d];
+                double sacc = fma(ja[i][d], ir, -Y[i] * u[d]);
 #pragma unroll
-                for (int c = r + 1; c < M; ++c) acc = fma(-A[r][c], du[c][d], acc);
-                du[r][d] = acc * ip;
+                for (int j = 0; j < i; ++j) sacc = fma(-Ln[i][j], du[j][d], sacc);
+                du[i][d] = sacc;
             }
-        }
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) du[i][d] *= Dinv[i];
+#pragma unroll
+        for (int i = M - 1; i >= 0; --i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double sacc = du[i][d];
+#pragma unroll
+                for (int j = i + 1; j < M; ++j) sacc = fma(-Ln[j][i], du[j][d], sacc);
+                du[i][d] = sacc;
+            }
     }
 
-    // chemistry
+    // Production rates rho_dot_a (Eq. (sumRhoDot)) of the mass-action
+    // mechanism.  With E_a = exp(g_a/(R_U T)) and act_a = c_a E_a, the
+    // rate of progress of a reaction is
+    //   q = k_f / prod_reac E * (prod_reac act - (P0/(r T))^(-dn) prod_prod act),
+    // which equals k_f prod_reac c - (k_f / K_c) prod_prod c.
     double wdot[M];
-    production_rates<M>(mc, rho_a, T, wdot, sh_chem);
-
-    // energy: q^eq, R^eq and the regularised quasi-equilibrium flux change
-    // Dq = (omega - omega_1)(q^* - q^eq) (Eqs. (gstareq1mom), (qdiff), (corrFourier))
-    double H = 0.0, HYdu[3] = {0, 0, 0};
-#pragma unroll
-    for (int s = 0; s < M; ++s) {
-        H = fma(Y[s], Ha[s], H);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) HYdu[d] = fma(Ha[s] * Y[s], du[s][d], HYdu[d]);
-    }
-    const double hk = H + 0.5 * usq;
-    double qeq[3], Dq[3];
     {
-        double Peq[6] = {P + rho * u[0] * u[0], P + rho * u[1] * u[1], P + rho * u[2] * u[2],
-                         rho * u[0] * u[1], rho * u[0] * u[2], rho * u[1] * u[2]};
-        double dP[3][3];
-        dP[0][0] = Pt[0] - Peq[0]; dP[1][1] = Pt[1] - Peq[1]; dP[2][2] = Pt[2] - Peq[2];
-        dP[0][1] = dP[1][0] = Pt[3] - Peq[3];
-        dP[0][2] = dP[2][0] = Pt[4] - Peq[4];
-        dP[1][2] = dP[2][1] = Pt[5] - Peq[5];
+        const double lnTr = lnT - mc.log_T_ref;
+        const double om_lnT = 1.0 - lnT;
+        double conc[M];
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            qeq[b] = hk * rho * u[b];
-            const double uP = u[0] * dP[0][b] + u[1] * dP[1][b] + u[2] * dP[2][b];
-            Dq[b] = (omega - omega1) * (q[b] - uP - qeq[b]) + omega1 * rho * HYdu[b] +
-                    0.5 * (2.0 - omega1) * P * HgY[b];
+        for (int s = 0; s < M; ++s) {
+            const double *gc = mc.gco[s];
+            const double g = fma(gc[0], om_lnT,
+                                 fma(fma(fma(fma(gc[4], T, gc[3]), T, gc[2]), T, gc[1]), T, fma(gc[5], invT, gc[6])));
+            conc[s] = rho_a[s] * mc.invW[s];
+            sh_g[s * LBMK_BLOCK + t] = g;
+            sh_act[s * LBMK_BLOCK + t] = conc[s] * exp(g);
+            sh_w[s * LBMK_BLOCK + t] = 0.0;
         }
-    }
-    // R^eq - rhoE theta I
-    const double Rt[6] = {hk * (P + rho * u[0] * u[0]) + P * u[0] * u[0] - rhoE / 3.0,
-                          hk * (P + rho * u[1] * u[1]) + P * u[1] * u[1] - rhoE / 3.0,
-                          hk * (P + rho * u[2] * u[2]) + P * u[2] * u[2] - rhoE / 3.0,
-                          (hk * rho + P) * u[0] * u[1], (hk * rho + P) * u[0] * u[2], (hk * rho + P) * u[1] * u[2]};
-    const double tr3 = (Rt[0] + Rt[1] + Rt[2]) * (1.0 / 3.0);
-
-    // sweep 2: collisions, direction by direction
-    Real Pe[M][3][3], Ps[M][3][3];
-    Real rhoR[M], KY[M], b2[M], bm1[M], wd[M];
+        const double c0 = mc.P0_over_r * invT, ic0 = T / mc.P0_over_r;   // P0/(r T) and its inverse
+        for (int k = 0; k < mc.R; ++k) {
+            double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k]));
+            const int nr = mc.nreac[k], np = mc.nprod[k];
+            double pf = 1.0;
+            for (int j = 0; j < nr; ++j) {
+                const int sidx = mc.reac[k][j] * LBMK_BLOCK + t;
+                arg -= sh_g[sidx];
+                pf *= sh_act[sidx];
+            }
+            double q = pf;
+            if (mc.rev[k]) {
+                double pr = 1.0;
+                for (int j = 0; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
+                const int dn = mc.dn[k];
+                for (int j = 0; j < dn; ++j) pr *= ic0;
+                for (int j = 0; j < -dn; ++j) pr *= c0;
+                q -= pr;
+            }
+            q *= exp(arg);
+            const int type = mc.rtype[k];
+            if (type != 0) {
+                double cM = 0.0;
 #pragma unroll
-    for (int s = 0; s < M; ++s) {
-        const Real zeta = (Real)(mc.Ra[s] * T);
+                for (int s = 0; s < M; ++s) cM = fma(mc.eff[k][s], conc[s], cM);
+                if (type == 1) {
+                    q *= cM;
+                } else {
+                    const double Pr = exp(fma(mc.dlow[k][1], lnTr, fma(-mc.dlow[k][2], invT, mc.dlow[k][0]))) * cM;
+                    q *= Pr / (1.0 + Pr);
+                }
+            }
+            for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * LBMK_BLOCK + t] -= q;
+            for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * LBMK_BLOCK + t] += q;
+        }
+#pragma unroll
+        for (int s = 0; s < M; ++s) wdot[s] = mc.W[s] * sh_w[s * LBMK_BLOCK + t];
+    }
+
+    // energy: equilibrium moments and the local part of
+    // Dq = (omega - omega_1)(q^* - q^eq) (Eqs. (gstareq1mom), (qdiff)); the
+    // grad-Y part (Eq. (corrFourier)) needs the neighbours and is added in k_step.
+    const double hk = H + 0.5 * usq;
+    double qeq[3], Rt[6], tr3;
+    energy_moments(rho, u, P, hk, sm.rhoE, qeq, Rt, tr3);
+    double dq[3];
+    {
+        const double dP[6] = {sm.P[0] - (P + rho * u[0] * u[0]), sm.P[1] - (P + rho * u[1] * u[1]),
+                              sm.P[2] - (P + rho * u[2] * u[2]), sm.P[3] - rho * u[0] * u[1],
+                              sm.P[4] - rho * u[0] * u[2], sm.P[5] - rho * u[1] * u[2]};
+        const double uP[3] = {u[0] * dP[0] + u[1] * dP[3] + u[2] * dP[4],
+                              u[0] * dP[3] + u[1] * dP[1] + u[2] * dP[5],
+                              u[0] * dP[4] + u[1] * dP[5] + u[2] * dP[2]};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            psi3((Real)u[d], zeta, Pe[s][d]);
-            psi3((Real)(u[d] + du[s][d]), zeta, Ps[s][d]);
+            double hyd = 0.0;
+#pragma unroll
+            for (int s = 0; s < M; ++s) hyd = fma(Ha[s] * Y[s], du[s][d], hyd);
+            dq[d] = (omega - omega1) * (sm.q[d] - uP[d] - qeq[d]) + omega1 * rho * hyd;
         }
-        rhoR[s] = (Real)rho_a[s];
-        KY[s] = (Real)(kappa * Y[s]);
-        const double beta = ita[s] / (2.0 + ita[s]);          // 1/(2 tau_a + 1), Eq. (fStar)
-        b2[s] = (Real)(2.0 * beta);
-        bm1[s] = (Real)(beta - 1.0);
-        wd[s] = (Real)wdot[s];
     }
-    Real Pm[3][3];
-    {
-        const Real zeta = (Real)(Rm * T);
-        for (int d = 0; d < 3; ++d) psi3((Real)u[d], zeta, Pm[d]);
-    }
-    const Real om = (Real)omega, rhoRl = (Real)rho;
-    const Real Xr[3] = {(Real)X[0], (Real)X[1], (Real)X[2]};
-    const Real gE = (Real)rhoE, gq[3] = {(Real)qeq[0], (Real)qeq[1], (Real)qeq[2]};
-    const Real gD[3] = {(Real)Dq[0], (Real)Dq[1], (Real)Dq[2]};
-    const Real gR[6] = {(Real)Rt[0], (Real)Rt[1], (Real)Rt[2], (Real)Rt[3], (Real)Rt[4], (Real)Rt[5]};
-    const Real gtr = (Real)tr3;
-    Real check = 0;
 
+    // the record: double rows
+    a.macro[DR_T * N + n] = T;
+    a.macro[(size_t)dr_ge(M) * N + n] = sm.rhoE;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a.macro[(size_t)(dr_gq(M) + d) * N + n] = qeq[d];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) a.macro[(size_t)(dr_gr(M) + d) * N + n] = Rt[d];
+    a.macro[(size_t)dr_gtr(M) * N + n] = tr3;
+#if LBMK_MIXED
+    // rest-direction equilibria of the species and mixture sets (Eqs. (feq), (feqmix))
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        const double z = (s < M - 1 ? mc.Ra[s] : Rm) * T;
+        const double r = s < M - 1 ? rho_a[s] : rho;
+        a.macro[(size_t)(DR_FEQ0 + s) * N + n] =
+            r * (1.0 - (u[0] * u[0] + z)) * (1.0 - (u[1] * u[1] + z)) * (1.0 - (u[2] * u[2] + z));
+    }
+#endif
+    // storage-type rows
+    const RecRows rr = rec_rows(M);
+    Real *R = rec(a);
+    R[(size_t)rr.nup * N + n] = (Real)nup;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        R[(size_t)(rr.phi + d) * N + n] = (Real)(rho * u[d] * (1.0 - 3.0 * Rm * T) - rho * u[d] * u[d] * u[d]);
+        R[(size_t)(rr.u + d) * N + n] = (Real)u[d];
+        R[(size_t)(rr.dq + d) * N + n] = (Real)dq[d];
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        R[(size_t)(rr.y + s) * N + n] = (Real)Y[s];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = (Real)du[s][d];
+        R[(size_t)(rr.wd + s) * N + n] = (Real)wdot[s];
+        // beta_a = 1/(2 tau_a + 1), Eq. (fStar)
+        const Real it = (Real)ita[s];
+        R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
+        R[(size_t)(rr.h + s) * N + n] = (Real)Ha[s];
+    }
+    R[(size_t)rr.rho * N + n] = (Real)rho;
+    R[(size_t)rr.kappa * N + n] = (Real)kappa;
+    R[(size_t)rr.rt * N + n] = (Real)(Rm * T);
+    R[(size_t)rr.om * N + n] = (Real)omega;
+    R[(size_t)rr.om1 * N + n] = (Real)omega1;
+    R[(size_t)rr.p * N + n] = (Real)P;
+}
+
+// ---------------------------------------------------------------------
+// Pass 2: G_alpha = (1/omega - 1/2) d_alpha Phi_alpha with the isotropic
+// gradient d_alpha phi = (1/theta) sum_i w_i c_ia phi(x + c_i).
+// ---------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const size_t N = a.N;
+    const RecRows rr = rec_rows(M);
+    Real *R = rec(a);
+    const Real *Phi = R + (size_t)rr.phi * N;
+    StencilIdx st;
+    make_stencil(st, nd, a);
+    Real d[3] = {0, 0, 0};
     for_dirs<0, LBMK_Q>([&](auto dd) {
         constexpr int I = decltype(dd)::value;
-        constexpr int ix = CX(I) + 1, iy = CY(I) + 1, iz = CZ(I) + 1;
+        const size_t nb = nb_of<I>(st);
+        if (CX(I)) d[0] += (Real)(WI(I) * CX(I)) * Phi[nb];
+        if (CY(I)) d[1] += (Real)(WI(I) * CY(I)) * Phi[N + nb];
+        if (CZ(I)) d[2] += (Real)(WI(I) * CZ(I)) * Phi[2 * N + nb];
+    });
+    const Real nup = R[(size_t)rr.nup * N + nd.n];
+    Real *G = R + (size_t)rr.g * N;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[k * N + nd.n] = nup * (Real)3 * d[k];
+}
+
+// ---------------------------------------------------------------------
+// Pass 3: the collisions, direction by direction.
+// ---------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
+{
+    const MechConst &mc = c_mech[a.slot];
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const int n = nd.n;
+    const size_t N = a.N;
+    const RecRows rr = rec_rows(M);
+    const Real *R = rec(a);
+    auto ld = [&](int row) { return R[(size_t)row * N + n]; };
+    auto ldd = [&](int row) { return a.macro[(size_t)row * N + n]; };
+
+    // X = -d_alpha G_alpha (Eq. (Xalpha)) and sum_a H_a grad Y_a (Eq. (corrFourier))
+    Real Hl[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) Hl[s] = ld(rr.h + s);
+    Real X[3] = {0, 0, 0}, HgY[3] = {0, 0, 0};
+    {
+        StencilIdx st;
+        make_stencil(st, nd, a);
+        const Real *G = R + (size_t)rr.g * N;
+        const Real *Yf = R + (size_t)rr.y * N;
+        for_dirs<0, LBMK_Q>([&](auto dd) {
+            constexpr int I = decltype(dd)::value;
+            if constexpr (I != REST) {
+                const size_t nb = nb_of<I>(st);
+                Real hy = 0;
+#pragma unroll
+                for (int s = 0; s < M; ++s) hy += Hl[s] * Yf[s * N + nb];
+                constexpr Real wx = (Real)(WI(I) * CX(I)), wy = (Real)(WI(I) * CY(I)), wz = (Real)(WI(I) * CZ(I));
+                if (CX(I)) { X[0] += wx * G[nb]; HgY[0] += wx * hy; }
+                if (CY(I)) { X[1] += wy * G[N + nb]; HgY[1] += wy * hy; }
+                if (CZ(I)) { X[2] += wz * G[2 * N + nb]; HgY[2] += wz * hy; }
+            }
+        });
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { X[k] *= (Real)-3; HgY[k] *= (Real)3; }
+    }
+
+    const Real rho = ld(rr.rho), om = ld(rr.om), om1 = ld(rr.om1), P = ld(rr.p);
+    const Real kappa = ld(rr.kappa), RT = ld(rr.rt);
+    const Real u[3] = {ld(rr.u), ld(rr.u + 1), ld(rr.u + 2)};
+    const Real T = (Real)ldd(DR_T);
+    Real gD[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gD[d] = ld(rr.dq + d) + (Real)0.5 * ((Real)2 - om1) * P * HgY[d];
+    // energy equilibrium moments in double (Eqs. (geq1mom), (geq2mom))
+    const double gE = ldd(dr_ge(M));
+    const double gq[3] = {ldd(dr_gq(M)), ldd(dr_gq(M) + 1), ldd(dr_gq(M) + 2)};
+    double gR[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) gR[d] = ldd(dr_gr(M) + d);
+    const double gtr = ldd(dr_gtr(M));
+
+    // per-species data: mass fraction, quasi-equilibrium velocity u + du_b,
+    // beta_b and rho_dot_b (densities, zeta and the products are formed per
+    // direction to keep the register footprint small)
+    Real Yl[M], xs[M][3], bt[M], wd[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        Yl[s] = ld(rr.y + s);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) xs[s][d] = u[d] + ld(rr.du + 3 * s + d);
+        bt[s] = ld(rr.beta + s);
+        wd[s] = ld(rr.wd + s);
+    }
+    const Real u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+
+    const PopView v = view(a.src, a);
+    PullIdx p;
+    make_pull(p, nd, a);
+    Real check = 0;
+
+#pragma unroll 1
+    for (int i = 0; i < LBMK_Q; ++i) {
+        const int cx = CX(i), cy = CY(i), cz = CZ(i);
+        const Src sr = src_of(i, p, a);
+        // energy set g, Eq. (g) in the regularised form
+        //   g + omega (g^eq - g) + w_i (Dq . c_i) / theta
+        {
+            const double g = sr.ghost ? load_ghost(a, sr.side, M, i, sr.idx) : load_g(v, i, sr.idx);
+            const double geq = grad_dir(i, gE, gq, gR, gtr);
+            const Real dq = (Real)cx * gD[0] + (Real)cy * gD[1] + (Real)cz * gD[2];
+            const double val = g + (double)(om * (Real)(geq - g) + (Real)(3.0 * WI(i)) * dq);
+            store_g(a.dst, a, i, n, val);
+            check += (Real)val;
+        }
+        if (LBMK_MIXED && i == REST) continue;     // rest of the species and mixture sets: below
         Real eqp[M], Dl[M];
 #pragma unroll
         for (int s = 0; s < M; ++s) {
-            eqp[s] = Pe[s][0][ix] * Pe[s][1][iy] * Pe[s][2][iz];
-            Dl[s] = rhoR[s] * (eqp[s] - Ps[s][0][ix] * Ps[s][1][iy] * Ps[s][2][iz]);
+            const Real z = RA(s) * T;
+            const Real pe = psi_c(cx, u[0], u2[0] + z) * psi_c(cy, u[1], u2[1] + z) * psi_c(cz, u[2], u2[2] + z);
+            const Real pst = psi_c(cx, xs[s][0], xs[s][0] * xs[s][0] + z) *
+                             psi_c(cy, xs[s][1], xs[s][1] * xs[s][1] + z) *
+                             psi_c(cz, xs[s][2], xs[s][2] * xs[s][2] + z);
+            eqp[s] = pe;
+            Dl[s] = rho * Yl[s] * (pe - pst);
         }
-        Real fv[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) fv[s] = absval<I>(mc, s, pull_raw<I>(src, gh, s, S, p, a));
-        Real outv[S];
+        // species a < M-1: Eq. (finalNumericalEquations) with F_ai of Eq. (fStar)
 #pragma unroll
         for (int s = 0; s < M - 1; ++s) {
             Real F = 0;
 #pragma unroll
             for (int b = 0; b < M; ++b)
                 if (b != s) F += INVWWD(s, b) * Dl[b];
-            F *= KY[s];
-            const Real feq = rhoR[s] * eqp[s];
-            const Real f = fv[s];
-            outv[s] = f + b2[s] * (feq - f) + bm1[s] * F + wd[s] * eqp[s];
+            F *= kappa * Yl[s];
+            const Real feq = rho * Yl[s] * eqp[s];
+            const Real f = sr.ghost ? (Real)load_ghost(a, sr.side, s, i, sr.idx) : load_sf(mc, v, s, i, sr.idx);
+            const Real val = f + (Real)2 * bt[s] * (feq - f) + (bt[s] - (Real)1) * F + wd[s] * eqp[s];
+            store_sf(mc, a.dst, a, s, i, n, (double)val);
+            check += val;
         }
+        // mixture f: Eq. (f) with the isotropy correction A_i . X (Eq. (Ai))
         {
-            const Real feq = rhoRl * Pm[0][ix] * Pm[1][iy] * Pm[2][iz];
-            Real AX = 0;
-            if (CX(I) * CX(I) + CY(I) * CY(I) + CZ(I) * CZ(I) == 1)
-                AX = (Real)0.5 * (CX(I) * Xr[0] + CY(I) * Xr[1] + CZ(I) * Xr[2]);
-            outv[M - 1] = fv[M - 1] + om * (feq - fv[M - 1]) + AX;
+            const Real feq = rho * psi_c(cx, u[0], u2[0] + RT) * psi_c(cy, u[1], u2[1] + RT) *
+                             psi_c(cz, u[2], u2[2] + RT);
+            const Real AX = (cx * cx + cy * cy + cz * cz == 1)
+                                ? (Real)0.5 * ((Real)cx * X[0] + (Real)cy * X[1] + (Real)cz * X[2]) : (Real)0;
+            const Real f = sr.ghost ? (Real)load_ghost(a, sr.side, M - 1, i, sr.idx)
+                                    : load_sf(mc, v, M - 1, i, sr.idx);
+            const Real val = f + om * (feq - f) + AX;
+            store_sf(mc, a.dst, a, M - 1, i, n, (double)val);
+            check += val;
         }
-        {
-            const Real qc = CX(I) * gq[0] + CY(I) * gq[1] + CZ(I) * gq[2];
-            const Real rcc = gR[0] * (CX(I) * CX(I)) + gR[1] * (CY(I) * CY(I)) + gR[2] * (CZ(I) * CZ(I)) +
-                             (Real)2 * (gR[3] * (CX(I) * CY(I)) + gR[4] * (CX(I) * CZ(I)) + gR[5] * (CY(I) * CZ(I)));
-            constexpr Real wi = (Real)WI(I);
-            const Real geq = wi * (gE + (Real)3 * qc + (Real)4.5 * (rcc - gtr));
-            const Real dq = CX(I) * gD[0] + CY(I) * gD[1] + CZ(I) * gD[2];
-            outv[M] = fv[M] + om * (geq - fv[M]) + (Real)3 * wi * dq;
+    }
+#if LBMK_MIXED
+    // Rest direction of the species and mixture sets: populations and
+    // equilibria in double, the collision increment (small near
+    // equilibrium) in float.
+    {
+        const double *rs = v.rest();
+        Real eqp[M], Dl[M];
+#pragma unroll
+        for (int s = 0; s < M; ++s) {
+            const Real z = RA(s) * T;
+            const Real pe = ((Real)1 - (u2[0] + z)) * ((Real)1 - (u2[1] + z)) * ((Real)1 - (u2[2] + z));
+            const Real pst = ((Real)1 - (xs[s][0] * xs[s][0] + z)) * ((Real)1 - (xs[s][1] * xs[s][1] + z)) *
+                             ((Real)1 - (xs[s][2] * xs[s][2] + z));
+            eqp[s] = pe;
+            Dl[s] = rho * Yl[s] * (pe - pst);
         }
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            put<I>(dst, mc, s, N, n, outv[s]);
-            check += outv[s];
+        for (int s = 0; s < M - 1; ++s) {
+            Real F = 0;
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+                if (b != s) F += INVWWD(s, b) * Dl[b];
+            F *= kappa * Yl[s];
+            const double f0 = rs[(size_t)s * N + n];
+            const Real diff = (Real)(ldd(DR_FEQ0 + s) - f0);
+            const double val = f0 + (double)((Real)2 * bt[s] * diff + (bt[s] - (Real)1) * F + wd[s] * eqp[s]);
+            store_sf(mc, a.dst, a, s, REST, n, val);
+            check += (Real)val;
         }
-    });
-    if (!isfinite(check)) flag(a, LBMK_BIT_NONFINITE);
+        const double f0 = rs[(size_t)(M - 1) * N + n];
+        const double val = f0 + (double)(om * (Real)(ldd(DR_FEQ0 + M - 1) - f0));
+        store_sf(mc, a.dst, a, M - 1, REST, n, val);
+        check += (Real)val;
+    }
+#endif
+    if (!isfinite(check)) flag(a.status, LBMK_BIT_NONFINITE);
 }
 
 // ---------------------------------------------------------------------
@@ -879,9 +1034,9 @@ int run_step(const StepArgs &a, cudaEvent_t *ev)
         k_ghost<M><<<grid_for(2 * plane), LBMK_BLOCK, 0, a.stream>>>(a);
     }
     if (ev) cudaEventRecord(ev[1], a.stream);
-    k_pre<M, false><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, 0u, nullptr);
+    k_pre<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[2], a.stream);
-    k_grad<<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
+    k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[3], a.stream);
     k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[4], a.stream);
@@ -895,7 +1050,7 @@ int run_moments(const StepArgs &a, unsigned mask, double *out)
         const int plane = a.ny * a.nz;
         k_ghost<M><<<grid_for(2 * plane), LBMK_BLOCK, 0, a.stream>>>(a);
     }
-    k_pre<M, true><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, mask, out);
+    k_moments<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, mask, out);
     return (int)cudaGetLastError();
 }
 

@@ -13,7 +13,10 @@ from pathlib import Path
 
 import numpy as np
 
-_LIB_PATH = Path(__file__).resolve().parent / "_build" / "liblbm.so"
+import os
+
+# LBM_LIBRARY may name another build of the same library (same ABI).
+_LIB_PATH = Path(os.environ.get("LBM_LIBRARY", Path(__file__).resolve().parent / "_build" / "liblbm.so"))
 if not _LIB_PATH.exists():
     raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2101_01702_gb300.build.build()")
 _lib = C.CDLL(str(_LIB_PATH))

@@ -40,8 +40,9 @@ def test_buffer_sizes_and_validation(lib):
     sp = lib.lbm_species(9, W.ctypes.data_as(C.POINTER(C.c_double)), 1, None, None, 298.15, None, None,
                          0.8, 0.71, p.species.r_lat, 1)
     pop, mac, gh = lib.lbm_buffer_sizes(lat, sp)
-    assert pop == 10 * 27 * 512 * 4
-    assert mac == (9 + 8) * 512 * 8
+    # species and mixture sets: float moving + double rest; energy set: double
+    assert pop == 9 * 27 * 512 * 4 + 9 * 512 * 8 + 27 * 512 * 8
+    assert mac == (9 + 12) * 512 * 8 + (19 + 7 * 9) * 512 * 4
     assert gh == 0
     lat.bc_x = 1
     lat.precision = lib.LBM_FP64
