@@ -199,10 +199,10 @@ def run_ours(args):
     mlups = N * args.steps * world / (ms * 1e-3) / 1e6
 
     # ---- per-kernel device times (CUDA events between the launches) -----
-    phases = s.step_timed(args.steps) / args.steps       # ms per launch: ghost, pre, grad, step
+    phases = s.step_timed(args.steps) / args.steps       # ms per launch: ghost, pre, chem, grad, step
     peak, peak_kind = _peaks()
     alg_bytes_node = 2 * S * 27 * store                  # one read + one write of every stored population
-    t_step = phases[3] * 1e-3
+    t_step = phases[4] * 1e-3
     achieved = alg_bytes_node * N / t_step / 1e9
     step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
 
@@ -261,8 +261,8 @@ def run_ours(args):
                        "parallelism": f"replicas{world}" if world > 1 else "single_gpu",
                        "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * S * 27 * store * N / 1e9)},
             "hbm_frac_step": step_frac,
-            "phase_ms": {"ghost": phases[0], "moments": phases[1], "gradients": phases[2],
-                         "collision": phases[3]},
+            "phase_ms": {"ghost": phases[0], "moments": phases[1], "chemistry": phases[2],
+                         "gradients": phases[3], "collision": phases[4]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step",
                          "peak_source": peak_kind,
@@ -271,7 +271,7 @@ def run_ours(args):
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * 3,
+            "gpu_launches": args.steps * 4,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

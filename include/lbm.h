@@ -158,9 +158,10 @@ int lbm_step(lbm_ctx *ctx, int n);
 int lbm_step_async(lbm_ctx *ctx, int n);
 
 /* lbm_step_async with CUDA events recorded on the stream between the
- * kernels of each step; after waiting, phase_ms[0..3] hold the summed
- * device time of the ghost-node, moment, gradient and collision kernels
- * over the n steps.  Returns like lbm_step. */
+ * kernels of each step; after waiting, phase_ms[0..LBM_PHASES-1] hold the
+ * summed device time of the ghost-node, moment, production-rate, gradient
+ * and collision kernels over the n steps.  Returns like lbm_step. */
+#define LBM_PHASES 5
 int lbm_step_timed(lbm_ctx *ctx, int n, double *phase_ms);
 
 /* Waits for the stream and returns (then clears) the recorded error. */
@@ -173,9 +174,11 @@ int lbm_sync(lbm_ctx *ctx);
  *   LBM_F_RHOE   rho E, 1 row         LBM_F_T     T, 1 row
  *   LBM_F_P      P = rho R T, 1 row   LBM_F_Y     Y_a, M rows
  *   LBM_F_J_A    species momenta rho_a u_a, 3M rows (a-major)
+ *   LBM_F_RHO_DOT  mass production rates rho_dot_a of the mechanism at
+ *                (rho_a, T), M rows (Eq. (sumRhoDot); per lattice time unit)
  * Waits for the stream before returning. */
 enum { LBM_F_RHO_A = 1, LBM_F_RHOU = 2, LBM_F_RHOE = 4, LBM_F_T = 8, LBM_F_P = 16,
-       LBM_F_Y = 32, LBM_F_J_A = 64 };
+       LBM_F_Y = 32, LBM_F_J_A = 64, LBM_F_RHO_DOT = 128 };
 int lbm_moments(lbm_ctx *ctx, unsigned mask, double *out);
 
 /* Number of doubles lbm_moments writes for mask. */

@@ -271,9 +271,9 @@ int lbm_step_async(lbm_ctx *c, int n)
 int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
 {
     if (!c || n < 0 || !phase_ms) return LBM_ERR_ARG;
-    for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
-    cudaEvent_t ev[5];
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < LBM_PHASES; ++k) phase_ms[k] = 0.0;
+    cudaEvent_t ev[LBM_PHASES + 1];
+    for (int k = 0; k <= LBM_PHASES; ++k)
         if (cudaEventCreate(&ev[k]) != cudaSuccess) {
             for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
             return LBM_ERR_CUDA;
@@ -284,14 +284,14 @@ int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
         const int e = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a, ev) : lbmk::step_fp64(a, ev);
         if (e) { st = LBM_ERR_CUDA; break; }
         c->cur = 1 - c->cur;
-        if (cudaEventSynchronize(ev[4]) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
-        for (int k = 0; k < 4; ++k) {
+        if (cudaEventSynchronize(ev[LBM_PHASES]) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
+        for (int k = 0; k < LBM_PHASES; ++k) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
             phase_ms[k] += ms;
         }
     }
-    for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+    for (int k = 0; k <= LBM_PHASES; ++k) cudaEventDestroy(ev[k]);
     if (st != LBM_OK) return st;
     return lbm_sync(c);
 }
@@ -328,12 +328,13 @@ size_t lbm_moments_count(const lbm_ctx *c, unsigned mask)
     if (mask & LBM_F_P) rows += 1;
     if (mask & LBM_F_Y) rows += c->M;
     if (mask & LBM_F_J_A) rows += 3 * (size_t)c->M;
+    if (mask & LBM_F_RHO_DOT) rows += c->M;
     return rows * (size_t)c->N;
 }
 
 int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
 {
-    if (!c || !out || mask == 0 || (mask & ~127u)) return LBM_ERR_ARG;
+    if (!c || !out || mask == 0 || (mask & ~255u)) return LBM_ERR_ARG;
     const size_t count = lbm_moments_count(c, mask);
     const bool dev = is_device_ptr(out);
     double *target = out;

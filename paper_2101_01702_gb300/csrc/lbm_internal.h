@@ -119,8 +119,9 @@ int upload_mixed(int slot, const MechConst &mc, cudaStream_t s);
 int init_fp64(const StepArgs &a, const double *X, const double *T, const double *u, double P);
 int init_mixed(const StepArgs &a, const double *X, const double *T, const double *u, double P);
 
-// one full time step src -> dst (ghost, moments, gradients, collision);
-// with ev != nullptr, events ev[0..4] are recorded around the four phases
+// one full time step src -> dst (ghost, moments, production rates,
+// gradients, collision); with ev != nullptr, events ev[0..5] are recorded
+// around the five phases
 int step_fp64(const StepArgs &a, cudaEvent_t *ev = nullptr);
 int step_mixed(const StepArgs &a, cudaEvent_t *ev = nullptr);
 

@@ -10,12 +10,13 @@
 // the Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
 // their equilibrium constants are double precision.
 //
-// One time step is four launches on one stream:
+// One time step is five launches on one stream:
 //   k_ghost  x-face ghost nodes (Sec. 5a; only for non-periodic x)
 //   k_pre    pull, all moments, Newton temperature, relaxation rates,
-//            Stefan-Maxwell diffusion velocities, production rates, the
-//            local part of the energy-flux correction and the energy
-//            equilibrium moments; writes the per-node record.
+//            Stefan-Maxwell diffusion velocities, the local part of the
+//            energy-flux correction and the energy equilibrium moments;
+//            writes the per-node record.
+//   k_chem   production rates of the reaction mechanism (record rows)
 //   k_grad   G_alpha = (1/omega - 1/2) d_alpha Phi_alpha (Eq. (Xalpha))
 //   k_step   pull again, X = -d_alpha G_alpha and sum_a H_a grad Y_a from the
 //            neighbours' records, and the collisions of
@@ -110,6 +111,23 @@ __device__ __forceinline__ Real load_sf(const MechConst &mc, const PopView &v, i
 #endif
 }
 
+// Stored value of species/mixture set s (< M), moving direction i, at
+// buffer node idx: in mixed precision the deviation from the rest state
+// RAWREF(s, i); the population is the stored value + RAWREF(s, i).
+__device__ __forceinline__ Real load_raw_sf(const PopView &v, int s, int i, size_t idx)
+{
+#if LBMK_MIXED
+    return __ldg(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx);
+#else
+    return __ldg(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
+#endif
+}
+#if LBMK_MIXED
+#define RAWREF(s_, i_) (mc.ref[s_][i_])
+#else
+#define RAWREF(s_, i_) ((Real)0)
+#endif
+
 // The same in double, keeping the double rest population exact.
 __device__ __forceinline__ double load_sf_d(const MechConst &mc, const PopView &v, int s, int i, size_t idx)
 {
@@ -181,7 +199,19 @@ __device__ __forceinline__ double pull_g(const PopView &v, const StepArgs &a, in
     return sr.ghost ? load_ghost(a, sr.side, a.M, i, sr.idx) : load_g(v, i, sr.idx);
 }
 
-// Writers of the post-collision state at node n.
+// Writers of the post-collision state at node n.  store_mov writes a
+// moving population of a species/mixture set in the storage precision
+// (no conversion through double); store_sf also takes the rest direction.
+__device__ __forceinline__ void store_mov(const MechConst &mc, void *buf, const StepArgs &a, int s, int i, size_t n,
+                                          Real v)
+{
+#if LBMK_MIXED
+    static_cast<float *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v - mc.ref[s][i];
+#else
+    static_cast<double *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v;
+#endif
+}
+
 __device__ __forceinline__ void store_sf(const MechConst &mc, void *buf, const StepArgs &a, int s, int i, size_t n,
                                          double v)
 {
@@ -378,7 +408,7 @@ struct Sums {
 
 template <int M, bool WITH_P>
 __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs &a, const PullIdx &p, int n,
-                                             double *rho_a, double (*ja)[3], Sums &sm)
+                                             double *rho_a, Real (*ja)[3], Sums &sm)
 {
     const PopView v = view(a.src, a);
 #pragma unroll
@@ -509,17 +539,107 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
 }
 
 // ---------------------------------------------------------------------
+// Production rates rho_dot_a (Eq. (sumRhoDot)) of the mass-action
+// mechanism.  With E_a = exp(g_a/(R_U T))
+// and act_a = c_a E_a, the rate of progress of a reaction is
+//   q = k_f / prod_reac E * (prod_reac act - (P0/(r T))^(-dn) prod_prod act),
+// which equals k_f prod_reac c - (k_f / K_c) prod_prod c.
+// ---------------------------------------------------------------------
+
+// Exponential of the rate expressions.  Double precision: exp().  Mixed
+// precision, where the rates are stored in float: a base-2 range reduction
+// done exactly in double (t = x log2(e) = k + f, k integer, |f| <= 1/2, in
+// the manner of Cody and Waite), 2^f from the hardware base-2 exponential
+// in float (ex2.approx, relative error about 2^-22), and 2^k added to the
+// binary exponent of the result; relative error below 5e-7.
+__device__ __forceinline__ double exp_rate(double x)
+{
+#if LBMK_MIXED
+    const double t = x * 1.4426950408889634074;          // log2(e)
+    if (!(fabs(t) < 1020.0)) return t > 0.0 ? (double)INFINITY : (t < 0.0 ? 0.0 : t);
+    const double k = rint(t);
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"((float)(t - k)));
+    const double r = (double)y;                          // in [2^-1/2, 2^1/2]
+    return __hiloint2double(__double2hiint(r) + (int)k * (1 << 20), __double2loint(r));
+#else
+    return exp(x);
+#endif
+}
+
+// Molar production rates sum_k (nu''_ak - nu'_ak) q_k at temperature T and
+// concentrations conc, left in sh_w[a * LBMK_BLOCK + t]; sh_act and sh_g
+// are this thread's scratch columns.
+template <int M>
+__device__ __forceinline__ void molar_production(const MechConst &mc, double T, const double *conc, double *sh_act,
+                                                 double *sh_g, Real *sh_w, int t)
+{
+    const double invT = 1.0 / T, lnT = log(T);
+    const double lnTr = lnT - mc.log_T_ref;
+    const double om_lnT = 1.0 - lnT;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        const double *gc = mc.gco[s];
+        const double g = fma(gc[0], om_lnT,
+                             fma(fma(fma(fma(gc[4], T, gc[3]), T, gc[2]), T, gc[1]), T, fma(gc[5], invT, gc[6])));
+        sh_g[s * LBMK_BLOCK + t] = g;
+        sh_act[s * LBMK_BLOCK + t] = conc[s] * exp_rate(g);
+        sh_w[s * LBMK_BLOCK + t] = 0;
+    }
+    const double c0 = mc.P0_over_r * invT, ic0 = T / mc.P0_over_r;   // P0/(r T) and its inverse
+    for (int k = 0; k < mc.R; ++k) {
+        double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k]));
+        const int nr = mc.nreac[k], np = mc.nprod[k];
+        double pf = 1.0;
+        for (int j = 0; j < nr; ++j) {
+            const int sidx = mc.reac[k][j] * LBMK_BLOCK + t;
+            arg -= sh_g[sidx];
+            pf *= sh_act[sidx];
+        }
+        double q = pf;
+        if (mc.rev[k]) {
+            double pr = 1.0;
+            for (int j = 0; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
+            const int dn = mc.dn[k];
+            for (int j = 0; j < dn; ++j) pr *= ic0;
+            for (int j = 0; j < -dn; ++j) pr *= c0;
+            q -= pr;
+        }
+        q *= exp_rate(arg);
+        const int type = mc.rtype[k];
+        if (type != 0) {
+            double cM = 0.0;
+#pragma unroll
+            for (int s = 0; s < M; ++s) cM = fma(mc.eff[k][s], conc[s], cM);
+            if (type == 1) {
+                q *= cM;
+            } else {
+                const double Pr = exp_rate(fma(mc.dlow[k][1], lnTr, fma(-mc.dlow[k][2], invT, mc.dlow[k][0]))) * cM;
+                q *= Pr / (1.0 + Pr);
+            }
+        }
+        const Real qr = (Real)q;
+        for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * LBMK_BLOCK + t] -= qr;
+        for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * LBMK_BLOCK + t] += qr;
+    }
+}
+
+// ---------------------------------------------------------------------
 // Moments for lbm_moments: the fields of the state in src (no record).
 // ---------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mask, double *out)
 {
+    __shared__ double sh_act[M * LBMK_BLOCK];
+    __shared__ double sh_g[M * LBMK_BLOCK];
+    __shared__ Real sh_w[M * LBMK_BLOCK];
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
     PullIdx p;
     make_pull(p, nd, a);
-    double rho_a[M], ja[M][3];
+    double rho_a[M];
+    Real ja[M][3];
     Sums sm;
     pull_moments<M, false>(mc, a, p, nd.n, rho_a, ja, sm);
     const double rho = sm.rho;
@@ -550,26 +670,31 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mas
         for (int s = 0; s < M - 1; ++s)
             for (int d = 0; d < 3; ++d) { out[(row + 3 * s + d) * N + n] = ja[s][d]; jM[d] -= ja[s][d]; }
         for (int d = 0; d < 3; ++d) out[(row + 3 * (M - 1) + d) * N + n] = jM[d];
+        row += 3 * M;
+    }
+    if (mask & 128u) {
+        double conc[M];
+#pragma unroll
+        for (int s = 0; s < M; ++s) conc[s] = rho_a[s] * mc.invW[s];
+        molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, threadIdx.x);
+        for (int s = 0; s < M; ++s) out[(row + s) * N + n] = mc.W[s] * (double)sh_w[s * LBMK_BLOCK + threadIdx.x];
     }
 }
 
 // ---------------------------------------------------------------------
-// Pass 1: pull, moments, temperature, relaxation, Stefan-Maxwell solve,
-// chemistry; writes the per-node record.
+// Pass 1: pull, moments, temperature, relaxation, Stefan-Maxwell solve;
+// writes the per-node record (all rows but the production rates).
 // ---------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
 {
-    __shared__ double sh_act[M * LBMK_BLOCK];   // c_a exp(g_a / R_U T)
-    __shared__ double sh_g[M * LBMK_BLOCK];     // g_a / R_U T
-    __shared__ double sh_w[M * LBMK_BLOCK];     // molar production
     const MechConst &mc = c_mech[a.slot];
-    const int t = threadIdx.x;
     Node nd;
     if (!node_of(nd, a)) return;
     PullIdx p;
     make_pull(p, nd, a);
-    double rho_a[M], ja[M][3];
+    double rho_a[M];
+    Real ja[M][3];
     Sums sm;
     pull_moments<M, true>(mc, a, p, nd.n, rho_a, ja, sm);
 
@@ -581,7 +706,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
     rho_a[M - 1] = rho - rest;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double js = sm.j[d];
+        Real js = (Real)sm.j[d];
 #pragma unroll
         for (int s = 0; s < M - 1; ++s) js -= ja[s][d];
         ja[M - 1][d] = js;
@@ -613,7 +738,6 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
     const double nup = nu_prime(mc, Rm, T);
     const double omega = 1.0 / (0.5 + nup);
     const double omega1 = 1.0 / (0.5 + nup / mc.Pr);
-    const double invT = 1.0 / T, lnT = log(T);
 
     // enthalpies, Eq. (specHa)
     double Ha[M], H = 0.0;
@@ -624,16 +748,24 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
     }
 
     // Eq. (tauab): 1/tau_ab = kappa / (W_a W_b D_ab), kappa = m R_U T;
-    // 1/tau_a = sum_b Y_b / tau_ab.
+    // 1/tau_a = sum_b Y_b / tau_ab.  From here to the diffusion velocities
+    // the arithmetic is in the storage type: in mixed precision these
+    // quantities are stored and used as floats, and the solve below is
+    // well conditioned (B is diagonally dominant after the symmetric
+    // scaling by Y).
     const double kappa = mc.r_lat * T / inv_m;
-    double ita[M];
+    const Real kap = (Real)kappa, irr = (Real)ir;
+    Real Yr[M], ur[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
+#pragma unroll
+    for (int s = 0; s < M; ++s) Yr[s] = (Real)Y[s];
+    Real ita[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        double acc = 0.0;
+        Real acc = 0;
 #pragma unroll
         for (int b = 0; b < M; ++b)
-            if (b != s) acc = fma(Y[b], mc.inv_WWD[s][b], acc);
-        ita[s] = kappa * acc;
+            if (b != s) acc = fma(Yr[b], INVWWD(s, b), acc);
+        ita[s] = kap * acc;
     }
 
     // Eq. (transform1), multiplied by Y_a so that the matrix is symmetric:
@@ -641,31 +773,31 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
     //   rhs_a = Y_a (u_a - u) = j_a / rho - Y_a u.
     // B is symmetric positive definite; L D L^T without pivoting, L unit
     // lower triangular (stored below the diagonal of Ln).
-    double du[M][3];
+    Real du[M][3];
     {
-        double Ln[M][M], D[M], Dinv[M];
+        Real Ln[M][M], D[M], Dinv[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const double hy = -0.5 * kappa * Y[i];
+            const Real hy = (Real)-0.5 * kap * Yr[i];
 #pragma unroll
-            for (int k = 0; k < i; ++k) Ln[i][k] = hy * mc.inv_WWD[i][k] * Y[k];
-            Ln[i][i] = Y[i] * fma(0.5, ita[i], 1.0);
+            for (int k = 0; k < i; ++k) Ln[i][k] = hy * INVWWD(i, k) * Yr[k];
+            Ln[i][i] = Yr[i] * fma((Real)0.5, ita[i], (Real)1);
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            double tk[M];
+            Real tk[M];
 #pragma unroll
             for (int j = 0; j < k; ++j) tk[j] = D[j] * Ln[k][j];
 #pragma unroll
             for (int i = k; i < M; ++i) {
-                double sacc = Ln[i][k];
+                Real sacc = Ln[i][k];
 #pragma unroll
                 for (int j = 0; j < k; ++j) sacc = fma(-Ln[i][j], tk[j], sacc);
                 Ln[i][k] = sacc;
             }
             D[k] = Ln[k][k];
-            if (!(D[k] > 0.0)) flag(a.status, LBMK_BIT_PIVOT);
-            Dinv[k] = 1.0 / D[k];
+            if (!(D[k] > (Real)0)) flag(a.status, LBMK_BIT_PIVOT);
+            Dinv[k] = (Real)1 / D[k];
 #pragma unroll
             for (int i = k + 1; i < M; ++i) Ln[i][k] *= Dinv[k];
         }
@@ -674,7 +806,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
         for (int i = 0; i < M; ++i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double sacc = fma(ja[i][d], ir, -Y[i] * u[d]);
+                Real sacc = fma(ja[i][d], irr, -Yr[i] * ur[d]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) sacc = fma(-Ln[i][j], du[j][d], sacc);
                 du[i][d] = sacc;
@@ -687,70 +819,11 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
         for (int i = M - 1; i >= 0; --i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                double sacc = du[i][d];
+                Real sacc = du[i][d];
 #pragma unroll
                 for (int j = i + 1; j < M; ++j) sacc = fma(-Ln[j][i], du[j][d], sacc);
                 du[i][d] = sacc;
             }
-    }
-
-    // Production rates rho_dot_a (Eq. (sumRhoDot)) of the mass-action
-    // mechanism.  With E_a = exp(g_a/(R_U T)) and act_a = c_a E_a, the
-    // rate of progress of a reaction is
-    //   q = k_f / prod_reac E * (prod_reac act - (P0/(r T))^(-dn) prod_prod act),
-    // which equals k_f prod_reac c - (k_f / K_c) prod_prod c.
-    double wdot[M];
-    {
-        const double lnTr = lnT - mc.log_T_ref;
-        const double om_lnT = 1.0 - lnT;
-        double conc[M];
-#pragma unroll
-        for (int s = 0; s < M; ++s) {
-            const double *gc = mc.gco[s];
-            const double g = fma(gc[0], om_lnT,
-                                 fma(fma(fma(fma(gc[4], T, gc[3]), T, gc[2]), T, gc[1]), T, fma(gc[5], invT, gc[6])));
-            conc[s] = rho_a[s] * mc.invW[s];
-            sh_g[s * LBMK_BLOCK + t] = g;
-            sh_act[s * LBMK_BLOCK + t] = conc[s] * exp(g);
-            sh_w[s * LBMK_BLOCK + t] = 0.0;
-        }
-        const double c0 = mc.P0_over_r * invT, ic0 = T / mc.P0_over_r;   // P0/(r T) and its inverse
-        for (int k = 0; k < mc.R; ++k) {
-            double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k]));
-            const int nr = mc.nreac[k], np = mc.nprod[k];
-            double pf = 1.0;
-            for (int j = 0; j < nr; ++j) {
-                const int sidx = mc.reac[k][j] * LBMK_BLOCK + t;
-                arg -= sh_g[sidx];
-                pf *= sh_act[sidx];
-            }
-            double q = pf;
-            if (mc.rev[k]) {
-                double pr = 1.0;
-                for (int j = 0; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
-                const int dn = mc.dn[k];
-                for (int j = 0; j < dn; ++j) pr *= ic0;
-                for (int j = 0; j < -dn; ++j) pr *= c0;
-                q -= pr;
-            }
-            q *= exp(arg);
-            const int type = mc.rtype[k];
-            if (type != 0) {
-                double cM = 0.0;
-#pragma unroll
-                for (int s = 0; s < M; ++s) cM = fma(mc.eff[k][s], conc[s], cM);
-                if (type == 1) {
-                    q *= cM;
-                } else {
-                    const double Pr = exp(fma(mc.dlow[k][1], lnTr, fma(-mc.dlow[k][2], invT, mc.dlow[k][0]))) * cM;
-                    q *= Pr / (1.0 + Pr);
-                }
-            }
-            for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * LBMK_BLOCK + t] -= q;
-            for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * LBMK_BLOCK + t] += q;
-        }
-#pragma unroll
-        for (int s = 0; s < M; ++s) wdot[s] = mc.W[s] * sh_w[s * LBMK_BLOCK + t];
     }
 
     // energy: equilibrium moments and the local part of
@@ -759,7 +832,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
     const double hk = H + 0.5 * usq;
     double qeq[3], Rt[6], tr3;
     energy_moments(rho, u, P, hk, sm.rhoE, qeq, Rt, tr3);
-    double dq[3];
+    Real dq[3];
     {
         const double dP[6] = {sm.P[0] - (P + rho * u[0] * u[0]), sm.P[1] - (P + rho * u[1] * u[1]),
                               sm.P[2] - (P + rho * u[2] * u[2]), sm.P[3] - rho * u[0] * u[1],
@@ -767,12 +840,16 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
         const double uP[3] = {u[0] * dP[0] + u[1] * dP[3] + u[2] * dP[4],
                               u[0] * dP[3] + u[1] * dP[1] + u[2] * dP[5],
                               u[0] * dP[4] + u[1] * dP[5] + u[2] * dP[2]};
+        Real HY[M];
+#pragma unroll
+        for (int s = 0; s < M; ++s) HY[s] = (Real)Ha[s] * Yr[s];
+        const Real orho = (Real)(omega1 * rho);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double hyd = 0.0;
+            Real hyd = 0;
 #pragma unroll
-            for (int s = 0; s < M; ++s) hyd = fma(Ha[s] * Y[s], du[s][d], hyd);
-            dq[d] = (omega - omega1) * (sm.q[d] - uP[d] - qeq[d]) + omega1 * rho * hyd;
+            for (int s = 0; s < M; ++s) hyd = fma(HY[s], du[s][d], hyd);
+            dq[d] = (Real)((omega - omega1) * (sm.q[d] - uP[d] - qeq[d])) + orho * hyd;
         }
     }
 
@@ -801,26 +878,51 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         R[(size_t)(rr.phi + d) * N + n] = (Real)(rho * u[d] * (1.0 - 3.0 * Rm * T) - rho * u[d] * u[d] * u[d]);
-        R[(size_t)(rr.u + d) * N + n] = (Real)u[d];
-        R[(size_t)(rr.dq + d) * N + n] = (Real)dq[d];
+        R[(size_t)(rr.u + d) * N + n] = ur[d];
+        R[(size_t)(rr.dq + d) * N + n] = dq[d];
     }
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        R[(size_t)(rr.y + s) * N + n] = (Real)Y[s];
+        R[(size_t)(rr.y + s) * N + n] = Yr[s];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = (Real)du[s][d];
-        R[(size_t)(rr.wd + s) * N + n] = (Real)wdot[s];
+        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = du[s][d];
         // beta_a = 1/(2 tau_a + 1), Eq. (fStar)
-        const Real it = (Real)ita[s];
+        const Real it = ita[s];
         R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
         R[(size_t)(rr.h + s) * N + n] = (Real)Ha[s];
     }
     R[(size_t)rr.rho * N + n] = (Real)rho;
-    R[(size_t)rr.kappa * N + n] = (Real)kappa;
+    R[(size_t)rr.kappa * N + n] = kap;
     R[(size_t)rr.rt * N + n] = (Real)(Rm * T);
     R[(size_t)rr.om * N + n] = (Real)omega;
     R[(size_t)rr.om1 * N + n] = (Real)omega1;
     R[(size_t)rr.p * N + n] = (Real)P;
+}
+
+// ---------------------------------------------------------------------
+// Pass 1b: production rates of the record's state (molar_production).
+// ---------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
+{
+    __shared__ double sh_act[M * LBMK_BLOCK];   // c_a exp(g_a / R_U T)
+    __shared__ double sh_g[M * LBMK_BLOCK];     // g_a / R_U T
+    __shared__ Real sh_w[M * LBMK_BLOCK];       // molar production
+    const MechConst &mc = c_mech[a.slot];
+    const int t = threadIdx.x;
+    const int n = blockIdx.x * blockDim.x + t;
+    if (n >= a.N) return;
+    const size_t N = a.N;
+    const RecRows rr = rec_rows(M);
+    Real *R = rec(a);
+    const double T = a.macro[DR_T * N + n];
+    const double rho = (double)R[(size_t)rr.rho * N + n];
+    double conc[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) conc[s] = rho * (double)R[(size_t)(rr.y + s) * N + n] * mc.invW[s];
+    molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, t);
+#pragma unroll
+    for (int s = 0; s < M; ++s) R[(size_t)(rr.wd + s) * N + n] = (Real)mc.W[s] * sh_w[s * LBMK_BLOCK + t];
 }
 
 // ---------------------------------------------------------------------
@@ -858,6 +960,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
 {
+    __shared__ double sh_B[LBMK_Q * LBMK_BLOCK];   // B_i of the energy-set collision
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
@@ -924,34 +1027,119 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
     }
     const Real u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
 
+    // Energy set, Eq. (g) in the regularised form: the post-collision value
+    // is (1 - omega) g_i + B_i with
+    //   B_i = omega g_i^eq + 3 w_i c_i . Dq
+    //       = w_i [A0 + c_i . A1 + sum_d c_id^2 A2_d + sum_{d<e} c_id c_ie A3_de],
+    //   A0 = omega (rho E - (9/2) tr3),  A1 = 3 (omega q^eq + Dq),
+    //   A2_d = (9/2) omega R_dd,         A3_de = 9 omega R_de,
+    // R = R^eq - rho E theta I (Eq. (gieq) expanded in c_i).
+    const double omd = (double)om, om1m = 1.0 - omd;
+    const double A0 = omd * (gE - 4.5 * gtr);
+    double A1[3], A2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        A1[d] = 3.0 * fma(omd, gq[d], (double)gD[d]);
+        A2[d] = 4.5 * omd * gR[d];
+    }
+    const double A3xy = 9.0 * omd * gR[3], A3xz = 9.0 * omd * gR[4], A3yz = 9.0 * omd * gR[5];
+    // B_i of the 27 directions, kept in this thread's column of shared memory
+    for_dirs<0, 9>([&](auto dj) {
+        constexpr int j = decltype(dj)::value, cy = j % 3 - 1, cz = j / 3 - 1;
+        constexpr int nnz = (cy != 0) + (cz != 0);
+        double base = A0, lin = A1[0];
+        if (cy) { base += cy * A1[1] + A2[1]; lin += cy * A3xy; }
+        if (cz) { base += cz * A1[2] + A2[2]; lin += cz * A3xz; }
+        if (cy && cz) base += (cy * cz) * A3yz;
+        // w_i = w(cx) w(cy) w(cz) with w(0) = 2/3, w(+-1) = 1/6
+        constexpr double w0 = nnz == 0 ? 8.0 / 27.0 : (nnz == 1 ? 2.0 / 27.0 : 1.0 / 54.0);
+        constexpr double w1 = nnz == 0 ? 2.0 / 27.0 : (nnz == 1 ? 1.0 / 54.0 : 1.0 / 216.0);
+        const double bq = base + A2[0];
+        sh_B[(3 * j) * LBMK_BLOCK + threadIdx.x] = w1 * (bq - lin);
+        sh_B[(3 * j + 1) * LBMK_BLOCK + threadIdx.x] = w0 * base;
+        sh_B[(3 * j + 2) * LBMK_BLOCK + threadIdx.x] = w1 * (bq + lin);
+    });
+
     const PopView v = view(a.src, a);
     PullIdx p;
     make_pull(p, nd, a);
     Real check = 0;
+    double gcheck = 0.0;
 
+    // Directions row by row: j = (cy+1) + 3 (cz+1), then cx = -1, 0, 1
+    // (direction i = (cx+1) + 3 j, i.e. i = 0..26 in order).  The y-z
+    // factors of the product-form equilibria are formed once per row.  In mixed precision the populations of direction
+    // i+1 are loaded while direction i is collided (raw stored values; the
+    // rest state is added where they are used).
+    constexpr bool kPrefetch = LBMK_MIXED;
+    Real fraw[M];
+    double graw = 0.0;
+    auto load_raw = [&](int i) {
+        const Src sr = src_of(i, p, a);
+        if (sr.ghost) {
+            graw = load_ghost(a, sr.side, M, i, sr.idx);
+#pragma unroll
+            for (int s = 0; s < M; ++s) fraw[s] = (Real)load_ghost(a, sr.side, s, i, sr.idx) - RAWREF(s, i);
+        } else {
+            graw = load_g(v, i, sr.idx);
+            if (LBMK_MIXED && i == REST) return;
+#pragma unroll
+            for (int s = 0; s < M; ++s) fraw[s] = load_raw_sf(v, s, i, sr.idx);
+        }
+    };
+    if (kPrefetch) load_raw(0);
+
+    Real pe_yz[M], ps_yz[M], fe_yz = 0, AXyz = 0;
+    int cy = 0, cz = 0;
+    auto yz_factors = [&](int s, Real z, Real &pe, Real &ps) {
+        pe = psi_c(cy, u[1], u2[1] + z) * psi_c(cz, u[2], u2[2] + z);
+        ps = psi_c(cy, xs[s][1], xs[s][1] * xs[s][1] + z) * psi_c(cz, xs[s][2], xs[s][2] * xs[s][2] + z);
+    };
 #pragma unroll 1
     for (int i = 0; i < LBMK_Q; ++i) {
-        const int cx = CX(i), cy = CY(i), cz = CZ(i);
-        const Src sr = src_of(i, p, a);
-        // energy set g, Eq. (g) in the regularised form
-        //   g + omega (g^eq - g) + w_i (Dq . c_i) / theta
-        {
-            const double g = sr.ghost ? load_ghost(a, sr.side, M, i, sr.idx) : load_g(v, i, sr.idx);
-            const double geq = grad_dir(i, gE, gq, gR, gtr);
-            const Real dq = (Real)cx * gD[0] + (Real)cy * gD[1] + (Real)cz * gD[2];
-            const double val = g + (double)(om * (Real)(geq - g) + (Real)(3.0 * WI(i)) * dq);
-            store_g(a.dst, a, i, n, val);
-            check += (Real)val;
+        const int cx = i % 3 - 1, j = i / 3;
+        if (cx < 0) {
+            cy = j % 3 - 1;
+            cz = j / 3 - 1;
+            const int nnz = (cy != 0) + (cz != 0);
+            // y-z factors of the species equilibria: kept across the row in
+            // float; recomputed per direction in double (register budget)
+            if (LBMK_MIXED) {
+#pragma unroll
+                for (int s = 0; s < M; ++s) yz_factors(s, RA(s) * T, pe_yz[s], ps_yz[s]);
+            }
+            fe_yz = rho * psi_c(cy, u[1], u2[1] + RT) * psi_c(cz, u[2], u2[2] + RT);
+            // isotropy correction A_i . X (Eq. (Ai)): only |c_i| = 1
+            AXyz = nnz == 1 ? (Real)0.5 * ((Real)cy * X[1] + (Real)cz * X[2]) : (Real)0;
         }
-        if (LBMK_MIXED && i == REST) continue;     // rest of the species and mixture sets: below
+        Real fc[M];
+        double gc;
+        if (kPrefetch) {
+#pragma unroll
+            for (int s = 0; s < M; ++s) fc[s] = fraw[s];
+            gc = graw;
+            if (i + 1 < LBMK_Q) load_raw(i + 1);
+        } else {
+            load_raw(i);
+#pragma unroll
+            for (int s = 0; s < M; ++s) fc[s] = fraw[s];
+            gc = graw;
+        }
+        {
+            const double val = fma(om1m, gc, sh_B[i * LBMK_BLOCK + threadIdx.x]);
+            store_g(a.dst, a, i, n, val);
+            gcheck += val;
+        }
+        if (LBMK_MIXED && i == REST) continue;   // rest of the species and mixture sets: below
         Real eqp[M], Dl[M];
 #pragma unroll
         for (int s = 0; s < M; ++s) {
             const Real z = RA(s) * T;
-            const Real pe = psi_c(cx, u[0], u2[0] + z) * psi_c(cy, u[1], u2[1] + z) * psi_c(cz, u[2], u2[2] + z);
-            const Real pst = psi_c(cx, xs[s][0], xs[s][0] * xs[s][0] + z) *
-                             psi_c(cy, xs[s][1], xs[s][1] * xs[s][1] + z) *
-                             psi_c(cz, xs[s][2], xs[s][2] * xs[s][2] + z);
+            Real pyz, syz;
+            if (LBMK_MIXED) { pyz = pe_yz[s]; syz = ps_yz[s]; }
+            else yz_factors(s, z, pyz, syz);
+            const Real pe = psi_c(cx, u[0], u2[0] + z) * pyz;
+            const Real pst = psi_c(cx, xs[s][0], xs[s][0] * xs[s][0] + z) * syz;
             eqp[s] = pe;
             Dl[s] = rho * Yl[s] * (pe - pst);
         }
@@ -964,21 +1152,18 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
                 if (b != s) F += INVWWD(s, b) * Dl[b];
             F *= kappa * Yl[s];
             const Real feq = rho * Yl[s] * eqp[s];
-            const Real f = sr.ghost ? (Real)load_ghost(a, sr.side, s, i, sr.idx) : load_sf(mc, v, s, i, sr.idx);
+            const Real f = fc[s] + RAWREF(s, i);
             const Real val = f + (Real)2 * bt[s] * (feq - f) + (bt[s] - (Real)1) * F + wd[s] * eqp[s];
-            store_sf(mc, a.dst, a, s, i, n, (double)val);
+            store_mov(mc, a.dst, a, s, i, n, val);
             check += val;
         }
         // mixture f: Eq. (f) with the isotropy correction A_i . X (Eq. (Ai))
         {
-            const Real feq = rho * psi_c(cx, u[0], u2[0] + RT) * psi_c(cy, u[1], u2[1] + RT) *
-                             psi_c(cz, u[2], u2[2] + RT);
-            const Real AX = (cx * cx + cy * cy + cz * cz == 1)
-                                ? (Real)0.5 * ((Real)cx * X[0] + (Real)cy * X[1] + (Real)cz * X[2]) : (Real)0;
-            const Real f = sr.ghost ? (Real)load_ghost(a, sr.side, M - 1, i, sr.idx)
-                                    : load_sf(mc, v, M - 1, i, sr.idx);
+            const Real feq = psi_c(cx, u[0], u2[0] + RT) * fe_yz;
+            const Real AX = cx == 0 ? AXyz : (j == 4 ? (Real)0.5 * (Real)cx * X[0] : (Real)0);
+            const Real f = fc[M - 1] + RAWREF(M - 1, i);
             const Real val = f + om * (feq - f) + AX;
-            store_sf(mc, a.dst, a, M - 1, i, n, (double)val);
+            store_mov(mc, a.dst, a, M - 1, i, n, val);
             check += val;
         }
     }
@@ -1017,7 +1202,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
         check += (Real)val;
     }
 #endif
-    if (!isfinite(check)) flag(a.status, LBMK_BIT_NONFINITE);
+    if (!isfinite(check) || !isfinite(gcheck)) flag(a.status, LBMK_BIT_NONFINITE);
 }
 
 // ---------------------------------------------------------------------
@@ -1036,10 +1221,12 @@ int run_step(const StepArgs &a, cudaEvent_t *ev)
     if (ev) cudaEventRecord(ev[1], a.stream);
     k_pre<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[2], a.stream);
-    k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
+    k_chem<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[3], a.stream);
-    k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
+    k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[4], a.stream);
+    k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
+    if (ev) cudaEventRecord(ev[5], a.stream);
     return (int)cudaGetLastError();
 }
 

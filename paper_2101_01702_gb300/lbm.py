@@ -34,6 +34,8 @@ LBM_BC_EQ_ZEROGRAD_U0LEFT = 1
 LBM_FP64 = 0
 LBM_MIXED = 1
 LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2, 4, 8, 16, 32, 64
+LBM_F_RHO_DOT = 128
+LBM_PHASES = 5
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -133,7 +135,7 @@ def lbm_step_async(ctx, n: int) -> int:
 
 
 def lbm_step_timed(ctx, n: int, phase_ms: np.ndarray) -> int:
-    assert phase_ms.dtype == np.float64 and phase_ms.size >= 4
+    assert phase_ms.dtype == np.float64 and phase_ms.size >= LBM_PHASES
     return _lib.lbm_step_timed(ctx, int(n), phase_ms.ctypes.data_as(_dp))
 
 
@@ -271,8 +273,8 @@ class Solver:
 
     def step_timed(self, n: int = 1):
         """Runs n steps; returns per-phase device milliseconds summed over
-        them (ghost, moments, gradients, collision)."""
-        ph = np.zeros(4)
+        them (ghost, moments, production rates, gradients, collision)."""
+        ph = np.zeros(LBM_PHASES)
         _check(lbm_step_timed(self.ctx, n, ph), "lbm_step_timed")
         return ph
 
@@ -291,7 +293,8 @@ class Solver:
             _check(lbm_moments(self.ctx, mask, out.ctypes.data), "lbm_moments")
         res, row, N, M = {}, 0, self.N, self.M
         for bit, name, rows in ((LBM_F_RHO_A, "rho_a", M), (LBM_F_RHOU, "rhou", 3), (LBM_F_RHOE, "rhoE", 1),
-                                (LBM_F_T, "T", 1), (LBM_F_P, "P", 1), (LBM_F_Y, "Y", M), (LBM_F_J_A, "j_a", 3 * M)):
+                                (LBM_F_T, "T", 1), (LBM_F_P, "P", 1), (LBM_F_Y, "Y", M), (LBM_F_J_A, "j_a", 3 * M),
+                                (LBM_F_RHO_DOT, "rho_dot", M)):
             if mask & bit:
                 blk = out[row * N:(row + rows) * N]
                 res[name] = blk.reshape(rows, N) if rows > 1 else blk.reshape(N)
