@@ -30,6 +30,32 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MLUPS (M+2 pop sets + chemistry), mixed vs FP64 step, % of HBM roofline"
 FALLBACK_HBM_GBS = 6800.0
 
+# FP64 arithmetic peak of the GPU: 152 SMs x 2 FP64 FMA per SM and clock
+# x 2 flops x 2070 MHz (maximum SM clock).
+SM_COUNT, FP64_FMA_PER_SM_CLK, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# Per lattice node and launch, counted by ncu on the 128^3 instance of this
+# workload for the kernels as they stand (profiles/ has the captures):
+#   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions;
+#   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
+FP64_FLOPS_PER_NODE = {
+    "mixed": {"k_pre": 747.0, "k_chem": 679.0, "k_step": 217.0},
+    "fp64": {"k_pre": 2859.4, "k_chem": 1630.0, "k_step": 17441.0},
+}
+DRAM_BYTES_PER_NODE = {
+    "mixed": {"k_pre": 2200.3, "k_chem": 64.4, "k_step": 2955.4},
+    "fp64": {"k_pre": 3410.3, "k_chem": 138.2, "k_step": 5148.7},
+}
+
+
+def stored_bytes_per_node(M: int, mixed: bool) -> int:
+    """Bytes of one copy of the stored state per node: in mixed precision the
+    26 moving populations of the M species/mixture sets in float, their rest
+    populations and the 27 energy populations in double; otherwise all
+    (M+1) x 27 populations in double."""
+    return M * 26 * 4 + M * 8 + 27 * 8 if mixed else (M + 1) * 27 * 8
+
 
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
@@ -170,7 +196,6 @@ def run_ours(args):
     M = prob.species.M
     S = M + 1
     precision = lbm.LBM_MIXED if args.precision == "mixed" else lbm.LBM_FP64
-    store = 4 if precision == lbm.LBM_MIXED else 8
     stream = torch.cuda.Stream()
 
     def timed_steps(solver, K):
@@ -188,23 +213,56 @@ def run_ours(args):
         return e0.elapsed_time(e1)
 
     # ---- device-resident run (value) ------------------------------------
+    # The timed region: K steps enqueued back to back on the library's
+    # stream with CUDA events between the kernels (one wait at the end);
+    # the events give the whole-run time and each kernel's launch times.
     s = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
     s.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
     with ClockSampler(local) as clk:
-        ms = timed_steps(s, args.steps)
+        ph = s.step_timed(args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    ms = float(ph[lbm.LBM_PHASES])
+    phases = ph[:lbm.LBM_PHASES] / args.steps            # ms per launch: ghost, pre, chem, grad, step
     ms_t = torch.tensor([ms], device="cuda")
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
     mlups = N * args.steps * world / (ms * 1e-3) / 1e6
 
-    # ---- per-kernel device times (CUDA events between the launches) -----
-    phases = s.step_timed(args.steps) / args.steps       # ms per launch: ghost, pre, chem, grad, step
+    # ---- rooflines --------------------------------------------------------
+    # The step is bound by FP64 arithmetic (temperature iteration, energy
+    # moments, reaction rates): the roofline of the longest kernel is the
+    # FP64 one.  The HBM view of the whole step counts one read and one write
+    # of the stored state per node.
     peak, peak_kind = _peaks()
-    alg_bytes_node = 2 * S * 27 * store                  # one read + one write of every stored population
-    t_step = phases[4] * 1e-3
-    achieved = alg_bytes_node * N / t_step / 1e9
+    mixed = precision == lbm.LBM_MIXED
+    alg_bytes_node = 2 * stored_bytes_per_node(M, mixed)
     step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
+    kern_ms = {"k_pre": phases[1], "k_chem": phases[2], "k_grad": phases[3], "k_step": phases[4]}
+    flops = FP64_FLOPS_PER_NODE[args.precision]
+    dram = DRAM_BYTES_PER_NODE[args.precision]
+    kernels = {}
+    for k, t in kern_ms.items():
+        e = {"ms": t}
+        if flops.get(k):
+            e["fp64_tflops"] = flops[k] * N / (t * 1e-3) / 1e12
+            e["fp64_frac"] = e["fp64_tflops"] / FP64_PEAK_TFLOPS
+        if dram.get(k):
+            e["dram_gbs"] = dram[k] * N / (t * 1e-3) / 1e9
+        kernels[k] = e
+    dom = max(("k_pre", "k_chem", "k_step"), key=lambda k: kern_ms[k])
+    roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom].get("fp64_tflops"),
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kernels[dom].get("fp64_frac"),
+                "traffic": dram[dom] * N if dram.get(dom) else None,
+                "flops_per_node": flops.get(dom),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"}
+    roofline_hbm = {"bound": "hbm", "kernel": "whole step",
+                    "achieved": alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9, "peak": peak,
+                    "unit": "GB/s", "frac": step_frac, "algorithmic_bytes_per_node": alg_bytes_node,
+                    "peak_source": peak_kind}
 
     # ---- end to end through the C ABI with host buffers ------------------
     e2e = None
@@ -241,7 +299,7 @@ def run_ours(args):
         k64 = max(2, args.steps // 2)
         ms64 = timed_steps(s64, k64)
         fp64 = {"mlups": N * k64 * world / (ms64 * 1e-3) / 1e6, "steps": k64,
-                "hbm_frac": 2 * S * 27 * 8 * N / (ms64 * 1e-3 / k64) / 1e9 / peak}
+                "hbm_frac": 2 * stored_bytes_per_node(M, False) * N / (ms64 * 1e-3 / k64) / 1e9 / peak}
         s64.close()
         del s64
         torch.cuda.empty_cache()
@@ -259,19 +317,19 @@ def run_ours(args):
             "config": {"workload": f"sphere3d_{n}^3_M9_{args.precision}", "nodes": N, "species": M,
                        "reactions": prob.mech.R, "stored_sets": S, "precision": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single_gpu",
-                       "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * S * 27 * store * N / 1e9)},
+                       "l2": "inputs larger than L2 (state %.1f GB per copy)"
+                             % (stored_bytes_per_node(M, mixed) * N / 1e9)},
             "hbm_frac_step": step_frac,
             "phase_ms": {"ghost": phases[0], "moments": phases[1], "chemistry": phases[2],
                          "gradients": phases[3], "collision": phases[4]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_step",
-                         "peak_source": peak_kind,
-                         "algorithmic_bytes_per_node": alg_bytes_node},
+            "roofline": roofline,
+            "roofline_hbm": roofline_hbm,
+            "kernels": kernels,
             "fp64_step": fp64,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * 4,
+            "gpu_launches": args.steps * (4 + (prob.lattice.bc_x != 0)),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -158,9 +158,12 @@ int lbm_step(lbm_ctx *ctx, int n);
 int lbm_step_async(lbm_ctx *ctx, int n);
 
 /* lbm_step_async with CUDA events recorded on the stream between the
- * kernels of each step; after waiting, phase_ms[0..LBM_PHASES-1] hold the
- * summed device time of the ghost-node, moment, production-rate, gradient
- * and collision kernels over the n steps.  Returns like lbm_step. */
+ * kernels of each step (all steps enqueued back to back, one wait at the
+ * end).  phase_ms must hold LBM_PHASES + 1 doubles: phase_ms[0..4] receive
+ * the summed device time of the ghost-node, moment, production-rate,
+ * gradient and collision kernels over the n steps, phase_ms[LBM_PHASES]
+ * the device time from the first launch to the end of the last.  Returns
+ * like lbm_step. */
 #define LBM_PHASES 5
 int lbm_step_timed(lbm_ctx *ctx, int n, double *phase_ms);
 

@@ -271,27 +271,40 @@ int lbm_step_async(lbm_ctx *c, int n)
 int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
 {
     if (!c || n < 0 || !phase_ms) return LBM_ERR_ARG;
-    for (int k = 0; k < LBM_PHASES; ++k) phase_ms[k] = 0.0;
-    cudaEvent_t ev[LBM_PHASES + 1];
-    for (int k = 0; k <= LBM_PHASES; ++k)
-        if (cudaEventCreate(&ev[k]) != cudaSuccess) {
-            for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
-            return LBM_ERR_CUDA;
-        }
+    for (int k = 0; k <= LBM_PHASES; ++k) phase_ms[k] = 0.0;
+    if (n == 0) return lbm_sync(c);
+    // LBM_PHASES + 1 events per step, all recorded before the one wait, so
+    // that the timed steps run back to back as in lbm_step_async.
+    const size_t nev = (size_t)n * (LBM_PHASES + 1);
+    cudaEvent_t *ev = (cudaEvent_t *)calloc(nev, sizeof(cudaEvent_t));
+    if (!ev) return LBM_ERR_ARG;
     int st = LBM_OK;
+    size_t made = 0;
+    for (; made < nev; ++made)
+        if (cudaEventCreate(&ev[made]) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
     for (int t = 0; t < n && st == LBM_OK; ++t) {
         StepArgs a = args_of(c);
-        const int e = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a, ev) : lbmk::step_fp64(a, ev);
-        if (e) { st = LBM_ERR_CUDA; break; }
+        cudaEvent_t *e = ev + (size_t)t * (LBM_PHASES + 1);
+        const int r = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a, e) : lbmk::step_fp64(a, e);
+        if (r) { st = LBM_ERR_CUDA; break; }
         c->cur = 1 - c->cur;
-        if (cudaEventSynchronize(ev[LBM_PHASES]) != cudaSuccess) { st = LBM_ERR_CUDA; break; }
+    }
+    if (st == LBM_OK && cudaEventSynchronize(ev[nev - 1]) != cudaSuccess) st = LBM_ERR_CUDA;
+    for (int t = 0; t < n && st == LBM_OK; ++t) {
+        cudaEvent_t *e = ev + (size_t)t * (LBM_PHASES + 1);
         for (int k = 0; k < LBM_PHASES; ++k) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            cudaEventElapsedTime(&ms, e[k], e[k + 1]);
             phase_ms[k] += ms;
         }
     }
-    for (int k = 0; k <= LBM_PHASES; ++k) cudaEventDestroy(ev[k]);
+    if (st == LBM_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[nev - 1]);
+        phase_ms[LBM_PHASES] = ms;
+    }
+    for (size_t k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+    free(ev);
     if (st != LBM_OK) return st;
     return lbm_sync(c);
 }

@@ -36,6 +36,17 @@ typedef double Real;
 #endif
 
 #define LBMK_BLOCK 128
+// Minimum resident blocks per SM asked of the compiler for the two large
+// kernels (register budget 65536 / (LBMK_BLOCK * minB)).  Measured on the
+// 256^3 nine-species lattice: the moment pass is latency bound and runs
+// fastest at 5 blocks (mixed; 96 registers, some spilled) and 3 blocks
+// (double; 168 registers); the collision pass runs fastest unconstrained.
+#ifndef LBMK_PRE_MINB
+#define LBMK_PRE_MINB (LBMK_MIXED ? 5 : 3)
+#endif
+#ifndef LBMK_STEP_MINB
+#define LBMK_STEP_MINB 1
+#endif
 #if LBMK_MIXED
 #define INVWWD(a_, b_) (mc.inv_WWD_f[a_][b_])
 #define RA(a_) (mc.Ra_f[a_])
@@ -686,7 +697,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mas
 // writes the per-node record (all rows but the production rates).
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_pre(StepArgs a)
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
 {
     const MechConst &mc = c_mech[a.slot];
     Node nd;
@@ -958,7 +969,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
 // Pass 3: the collisions, direction by direction.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_step(StepArgs a)
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 {
     __shared__ double sh_B[LBMK_Q * LBMK_BLOCK];   // B_i of the energy-set collision
     const MechConst &mc = c_mech[a.slot];

@@ -135,7 +135,7 @@ def lbm_step_async(ctx, n: int) -> int:
 
 
 def lbm_step_timed(ctx, n: int, phase_ms: np.ndarray) -> int:
-    assert phase_ms.dtype == np.float64 and phase_ms.size >= LBM_PHASES
+    assert phase_ms.dtype == np.float64 and phase_ms.size >= LBM_PHASES + 1
     return _lib.lbm_step_timed(ctx, int(n), phase_ms.ctypes.data_as(_dp))
 
 
@@ -273,8 +273,9 @@ class Solver:
 
     def step_timed(self, n: int = 1):
         """Runs n steps; returns per-phase device milliseconds summed over
-        them (ghost, moments, production rates, gradients, collision)."""
-        ph = np.zeros(LBM_PHASES)
+        them (ghost, moments, production rates, gradients, collision) and,
+        last, the device milliseconds of the whole run."""
+        ph = np.zeros(LBM_PHASES + 1)
         _check(lbm_step_timed(self.ctx, n, ph), "lbm_step_timed")
         return ph
 
