@@ -214,9 +214,10 @@ void *lbm_state_buffer(lbm_ctx *ctx);
  * process exits.  No context (lbm_create) is needed; the species and
  * mechanism tables are copied to constant memory on every call.
  * Limits: precision LBM_FP64 only (else LBM_ERR_UNSUPPORTED); the lattice
- * must fit, 256 + (22 + 7M) N 8 bytes plus, for non-periodic x,
- * 2 (M+1) 27 ny nz 8 bytes <= LBM_FIXED_SCRATCH_BYTES (e.g. 40^3 nodes
- * with M = 9, 64^3 with M = 3), else LBM_ERR_ARG.  The first call on a device looks up the array's device
+ * must fit, 256 + (31 + 8M) N 8 bytes plus, for non-periodic x,
+ * 2 (M+1) 27 ny nz 8 bytes <= LBM_FIXED_SCRATCH_BYTES (up to 43^3 nodes
+ * with M = 9, 53^3 with M = 3), else LBM_ERR_ARG.  The first call on a
+ * device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call uses the same array and it keeps the previous call's
  * contents (the call clears its status word itself), so calls that overlap

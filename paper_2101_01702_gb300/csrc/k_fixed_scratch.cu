@@ -26,7 +26,7 @@
 #include "lbm_pack.h"
 
 // Device-side scratch.  Layout of one call: [0, 256) status word, then the
-// macroscopic record (8 N (22 + 7M) bytes), then the x-face ghost planes.
+// macroscopic record (8 N (31 + 8M) bytes), then the x-face ghost planes.
 static __device__ __align__(256) unsigned char g_fixed_scratch[LBM_FIXED_SCRATCH_BYTES];
 
 namespace {

@@ -71,7 +71,10 @@ def test_fixed_scratch_step_matches_lbm_step(lbm, case):
 
 def test_fixed_scratch_rejects_lattices_beyond_the_array(lbm):
     import torch
-    prob = w.sphere3d_problem(n=80, radius=5.0)     # (9+8) * 80^3 * 8 B > 64 MiB
+    # the record takes (31 + 8 M) * 8 B per node: 44^3 nodes with M = 9 is the
+    # first cube beyond the 64 MiB array (43^3 fits); rejected before any
+    # device work, so the dummy buffers are never touched
+    prob = w.sphere3d_problem(n=44, radius=5.0)
     ref = lbm.Solver(prob.lattice, prob.species, prob.mech, precision=lbm.LBM_FP64)
     dummy = torch.empty(16, dtype=torch.float64, device="cuda")
     dummy2 = torch.empty(16, dtype=torch.float64, device="cuda")
