@@ -40,11 +40,13 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions;
 #   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 FP64_FLOPS_PER_NODE = {
-    "mixed": {"k_pre": 747.0, "k_chem": 679.0, "k_step": 217.0},
+    "mixed": {"k_pre": None, "k_chem": None, "k_step": None},
+    "mixed_fast": {"k_pre": 747.0, "k_chem": 679.0, "k_step": 217.0},
     "fp64": {"k_pre": 2859.4, "k_chem": 1630.0, "k_step": 17441.0},
 }
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2200.3, "k_chem": 64.4, "k_step": 2955.4},
+    "mixed": {"k_pre": None, "k_chem": None, "k_step": None},
+    "mixed_fast": {"k_pre": 2200.3, "k_chem": 64.4, "k_step": 2955.4},
     "fp64": {"k_pre": 3410.3, "k_chem": 138.2, "k_step": 5148.7},
 }
 
@@ -195,7 +197,8 @@ def run_ours(args):
     N = prob.lattice.n_nodes
     M = prob.species.M
     S = M + 1
-    precision = lbm.LBM_MIXED if args.precision == "mixed" else lbm.LBM_FP64
+    modes = {"mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST, "fp64": lbm.LBM_FP64}
+    precision = modes[args.precision]
     stream = torch.cuda.Stream()
 
     def timed_steps(solver, K):
@@ -238,7 +241,7 @@ def run_ours(args):
     # FP64 one.  The HBM view of the whole step counts one read and one write
     # of the stored state per node.
     peak, peak_kind = _peaks()
-    mixed = precision == lbm.LBM_MIXED
+    mixed = precision != lbm.LBM_FP64
     alg_bytes_node = 2 * stored_bytes_per_node(M, mixed)
     step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
     kern_ms = {"k_pre": phases[1], "k_chem": phases[2], "k_grad": phases[3], "k_step": phases[4]}
@@ -291,6 +294,26 @@ def run_ours(args):
     del s
     torch.cuda.empty_cache()
 
+    # ---- the fast mixed mode on the same lattice ---------------------------
+    fast = None
+    if not args.skip_fast and precision == lbm.LBM_MIXED:
+        sf = lbm.Solver.from_problem(prob, precision=lbm.LBM_MIXED_FAST, stream=stream)
+        sf.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        phf = sf.step_timed(args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        msf = float(phf[lbm.LBM_PHASES])
+        phf = phf[:lbm.LBM_PHASES] / args.steps
+        fast = {"mlups": N * args.steps * world / (msf * 1e-3) / 1e6, "steps": args.steps,
+                "phase_ms": {"moments": phf[1], "chemistry": phf[2], "gradients": phf[3], "collision": phf[4]},
+                "note": "LBM_MIXED_FAST: Stefan-Maxwell solve and relaxation in float, exponentials of the "
+                        "rates with a float 2^f; same storage and accuracy bar"}
+        sf.close()
+        del sf
+        torch.cuda.empty_cache()
+
     # ---- the double-precision step on the same lattice -------------------
     fp64 = None
     if not args.skip_fp64 and precision == lbm.LBM_MIXED:
@@ -313,7 +336,7 @@ def run_ours(args):
             "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if precision == lbm.LBM_MIXED else "f64", "data": "synthetic",
+            "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
             "config": {"workload": f"sphere3d_{n}^3_M9_{args.precision}", "nodes": N, "species": M,
                        "reactions": prob.mech.R, "stored_sets": S, "precision": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single_gpu",
@@ -325,6 +348,7 @@ def run_ours(args):
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "kernels": kernels,
+            "mixed_fast_step": fast,
             "fp64_step": fp64,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
@@ -344,8 +368,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=256)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_fast", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-fast", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args()

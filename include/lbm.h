@@ -47,7 +47,7 @@ enum {
 };
 
 enum { LBM_BC_PERIODIC = 0, LBM_BC_EQ_ZEROGRAD_U0LEFT = 1 };
-enum { LBM_FP64 = 0, LBM_MIXED = 1 };
+enum { LBM_FP64 = 0, LBM_MIXED = 1, LBM_MIXED_FAST = 2 };
 enum { LBM_THERMO_CONST_CP = 0, LBM_THERMO_POLY7 = 1 };
 enum { LBM_VISC_KINEMATIC = 0, LBM_VISC_RELAXATION = 1 };
 enum { LBM_RXN_ELEMENTARY = 0, LBM_RXN_THIRD_BODY = 1, LBM_RXN_FALLOFF = 2 };
@@ -57,10 +57,21 @@ enum { LBM_RXN_ELEMENTARY = 0, LBM_RXN_THIRD_BODY = 1, LBM_RXN_FALLOFF = 2 };
  * the equilibria of every set at the post-collision moments of the adjacent
  * boundary node, with zero velocity on the left (paper Sec. 5a, the 1D
  * flame setup); macroscopic fields used by the gradient stencils continue
- * with zero gradient.  precision = LBM_FP64 stores and collides in double;
- * LBM_MIXED stores populations as float deviations from per-set rest
- * states and collides in float, keeping double for the moments, the
- * temperature iteration, the Stefan-Maxwell solve and the chemistry. */
+ * with zero gradient.  precision:
+ *   LBM_FP64        stores and collides every population in double;
+ *   LBM_MIXED       stores the 26 moving populations of the species and
+ *                   mixture sets as float deviations from per-set rest
+ *                   states and collides them in float; their rest
+ *                   populations and the energy set stay double, and so do
+ *                   the moments, the temperature iteration, the
+ *                   Stefan-Maxwell solve, the reaction rates and the
+ *                   equilibrium constants;
+ *   LBM_MIXED_FAST  as LBM_MIXED, but the relaxation rates and the
+ *                   Stefan-Maxwell solve run in float and the exponentials
+ *                   of the rate expressions take a double range reduction
+ *                   with a float 2^f (relative error ~3e-7); its results
+ *                   are stored as floats in both mixed modes.  Same
+ *                   storage layout and accuracy bar as LBM_MIXED. */
 typedef struct {
     int nx, ny, nz;
     int bc_x;
@@ -120,15 +131,23 @@ typedef struct {
 } lbm_mechanism;
 
 /* Caller-owned device memory, sized by lbm_buffer_sizes():
- *   pop_a, pop_b  two population buffers, layout [M+1 sets][27][N], double
- *                 (LBM_FP64) or float deviations (LBM_MIXED); they swap roles
- *                 every step.  Must be distinct and 16-byte aligned.
- *   macro         per-node record: a row of doubles (temperature) then
- *                 21 + 7M rows of the storage type ([rows][N]): the
- *                 moments, relaxation rates, diffusion velocities,
- *                 production rates and gradient inputs of the current step.
- *   ghost         x-face ghost populations [2][M+1][27][ny*nz] in the
- *                 storage type; may be NULL for periodic x. */
+ *   pop_a, pop_b  two population buffers that swap roles every step; node
+ *                 n = x + nx (y + ny z); sets 0..M-2 the stored species,
+ *                 M-1 the mixture f, M the energy set g.
+ *                 LBM_FP64: double [M+1][27][N].
+ *                 mixed modes: float [M][27][N] (sets 0..M-1 as deviations
+ *                 from their rest states; the rest slot 13 unused), then at
+ *                 the next 16-byte boundary double [M][N] (their rest
+ *                 populations), then double [27][N] (the energy set).
+ *                 Must be distinct and 16-byte aligned.
+ *   macro         per-node record of the current step, [rows][N]: M+12
+ *                 rows of double (temperature first: the Newton starting
+ *                 point, which lbm_init writes), then 19+7M rows of the
+ *                 storage type (float in the mixed modes): moments,
+ *                 relaxation rates, diffusion velocities, production rates
+ *                 and the inputs of the gradient stencils.
+ *   ghost         x-face ghost populations, double [2][M+1][27][ny*nz];
+ *                 may be NULL for periodic x. */
 typedef struct {
     void *pop_a, *pop_b, *macro, *ghost;
     size_t pop_bytes, macro_bytes, ghost_bytes;

@@ -1,6 +1,6 @@
 """Builds the CUDA library liblbm.so for sm_103a (GB300) in-tree.
 
-nvcc compiles the three translation units in parallel and links them with
+nvcc compiles the translation units in parallel and links them with
 the static CUDA runtime; the result lands in paper_2101_01702_gb300/_build.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "liblbm.so"
-SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_fixed_scratch.cu"]
+SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_mixed_fast.cu", "k_fixed_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

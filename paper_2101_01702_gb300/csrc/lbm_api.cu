@@ -34,7 +34,16 @@ bool g_slot_used[LBMK_SLOTS] = {false, false, false, false};
 
 bool supported_M(int M) { return M == 2 || M == 3 || M == 9; }
 
-size_t store_size(int precision) { return precision == LBM_MIXED ? sizeof(float) : sizeof(double); }
+bool is_mixed(int precision) { return precision == LBM_MIXED || precision == LBM_MIXED_FAST; }
+bool valid_precision(int precision) { return precision == LBM_FP64 || is_mixed(precision); }
+size_t store_size(int precision) { return is_mixed(precision) ? sizeof(float) : sizeof(double); }
+
+const lbmk::PrecisionOps kOps[3] = {
+    {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64},
+    {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed},
+    {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast},
+};
+const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
 int map_status(unsigned bits)
 {
@@ -125,11 +134,11 @@ int lbm_buffer_sizes(const lbm_lattice *lat, const lbm_species *sp, size_t *pop_
 {
     if (!lat || !sp || lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || sp->M < 2 || sp->M > LBMK_MAXM)
         return LBM_ERR_ARG;
-    if (lat->precision != LBM_FP64 && lat->precision != LBM_MIXED) return LBM_ERR_ARG;
+    if (!valid_precision(lat->precision)) return LBM_ERR_ARG;
     const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
     const size_t S = (size_t)sp->M + 1;
     const size_t st = store_size(lat->precision);
-    if (pop_bytes) *pop_bytes = pop_bytes_for((int)S, N, lat->precision == LBM_MIXED);
+    if (pop_bytes) *pop_bytes = pop_bytes_for((int)S, N, is_mixed(lat->precision));
     if (macro_bytes) *macro_bytes = macro_bytes_for(sp->M, N, st);
     if (ghost_bytes) *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : ghost_bytes_for((int)S, (size_t)lat->ny * lat->nz);
     return LBM_OK;
@@ -188,8 +197,7 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     int st = check_cuda(cudaMalloc((void **)&c->status, 16));
     if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
     if (st == LBM_OK) {
-        const int e = lat->precision == LBM_MIXED ? lbmk::upload_mixed(slot, c->mc, c->stream)
-                                                  : lbmk::upload_fp64(slot, c->mc, c->stream);
+        const int e = ops(lat->precision).upload(slot, c->mc, c->stream);
         st = e ? LBM_ERR_CUDA : LBM_OK;
     }
     if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
@@ -208,7 +216,7 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
     const bool dX = is_device_ptr(X), dT = is_device_ptr(T), du = u ? is_device_ptr(u) : dX;
     if (dX != dT || dX != du) return LBM_ERR_ARG;     // all host or all device
     int st = LBM_OK;
-    if (c->lat.precision == LBM_MIXED) {
+    if (is_mixed(c->lat.precision)) {
         // rest states from the mean initial state
         const double *hX = X, *hT = T;
         double *tmpX = nullptr, *tmpT = nullptr;
@@ -223,7 +231,7 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
         }
         if (st == LBM_OK) {
             choose_references(c->mc, c->M, hX, hT, P, N);
-            st = lbmk::upload_mixed(c->slot, c->mc, c->stream) ? LBM_ERR_CUDA : LBM_OK;
+            st = ops(c->lat.precision).upload(c->slot, c->mc, c->stream) ? LBM_ERR_CUDA : LBM_OK;
         }
         free(tmpX);
         free(tmpT);
@@ -248,8 +256,7 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
     }
     StepArgs a = args_of(c);
     a.dst = c->buf[c->cur];
-    const int e = c->lat.precision == LBM_MIXED ? lbmk::init_mixed(a, dXp, dTp, dup, P)
-                                                : lbmk::init_fp64(a, dXp, dTp, dup, P);
+    const int e = ops(c->lat.precision).init(a, dXp, dTp, dup, P);
     if (e) return LBM_ERR_CUDA;
     st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
     if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
@@ -261,7 +268,7 @@ int lbm_step_async(lbm_ctx *c, int n)
     if (!c || n < 0) return LBM_ERR_ARG;
     for (int t = 0; t < n; ++t) {
         StepArgs a = args_of(c);
-        const int e = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a) : lbmk::step_fp64(a);
+        const int e = ops(c->lat.precision).step(a, nullptr);
         if (e) return LBM_ERR_CUDA;
         c->cur = 1 - c->cur;
     }
@@ -285,7 +292,7 @@ int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
     for (int t = 0; t < n && st == LBM_OK; ++t) {
         StepArgs a = args_of(c);
         cudaEvent_t *e = ev + (size_t)t * (LBM_PHASES + 1);
-        const int r = c->lat.precision == LBM_MIXED ? lbmk::step_mixed(a, e) : lbmk::step_fp64(a, e);
+        const int r = ops(c->lat.precision).step(a, e);
         if (r) { st = LBM_ERR_CUDA; break; }
         c->cur = 1 - c->cur;
     }
@@ -356,8 +363,7 @@ int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
         target = (double *)c->buf[1 - c->cur];
     }
     StepArgs a = args_of(c);
-    const int e = c->lat.precision == LBM_MIXED ? lbmk::moments_mixed(a, mask, target)
-                                                : lbmk::moments_fp64(a, mask, target);
+    const int e = ops(c->lat.precision).moments(a, mask, target);
     if (e) return LBM_ERR_CUDA;
     if (!dev) {
         int st = check_cuda(cudaMemcpyAsync(out, target, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

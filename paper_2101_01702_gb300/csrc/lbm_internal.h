@@ -115,17 +115,29 @@ struct StepArgs {
 namespace lbmk {
 int upload_fp64(int slot, const MechConst &mc, cudaStream_t s);
 int upload_mixed(int slot, const MechConst &mc, cudaStream_t s);
+int upload_mixed_fast(int slot, const MechConst &mc, cudaStream_t s);
 
 int init_fp64(const StepArgs &a, const double *X, const double *T, const double *u, double P);
 int init_mixed(const StepArgs &a, const double *X, const double *T, const double *u, double P);
+int init_mixed_fast(const StepArgs &a, const double *X, const double *T, const double *u, double P);
 
 // one full time step src -> dst (ghost, moments, production rates,
 // gradients, collision); with ev != nullptr, events ev[0..5] are recorded
 // around the five phases
 int step_fp64(const StepArgs &a, cudaEvent_t *ev = nullptr);
 int step_mixed(const StepArgs &a, cudaEvent_t *ev = nullptr);
+int step_mixed_fast(const StepArgs &a, cudaEvent_t *ev = nullptr);
 
 // macroscopic fields of the state in src, written to out (device)
 int moments_fp64(const StepArgs &a, unsigned mask, double *out);
 int moments_mixed(const StepArgs &a, unsigned mask, double *out);
+int moments_mixed_fast(const StepArgs &a, unsigned mask, double *out);
+
+// The kernel unit of one storage/arithmetic precision.
+struct PrecisionOps {
+    int (*upload)(int slot, const MechConst &mc, cudaStream_t s);
+    int (*init)(const StepArgs &a, const double *X, const double *T, const double *u, double P);
+    int (*step)(const StepArgs &a, cudaEvent_t *ev);
+    int (*moments)(const StepArgs &a, unsigned mask, double *out);
+};
 }  // namespace lbmk

@@ -29,10 +29,28 @@
 
 #include "lbm_internal.h"
 
+#ifndef LBMK_FAST
+#define LBMK_FAST 0
+#endif
+
 #if LBMK_MIXED
 typedef float Real;
 #else
 typedef double Real;
+#endif
+// SReal: the relaxation rates, the Stefan-Maxwell factorisation and solve
+// and the diffusion part of the energy-flux correction; WReal: the
+// accumulation of the reaction contributions.  Double except in the fast
+// mixed unit (LBMK_FAST), where these results, stored as floats, are also
+// computed in float.
+#if LBMK_MIXED && LBMK_FAST
+typedef float SReal;
+typedef float WReal;
+#define INVWWD_S(a_, b_) (mc.inv_WWD_f[a_][b_])
+#else
+typedef double SReal;
+typedef double WReal;
+#define INVWWD_S(a_, b_) (mc.inv_WWD[a_][b_])
 #endif
 
 #define LBMK_BLOCK 128
@@ -557,15 +575,15 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
 // which equals k_f prod_reac c - (k_f / K_c) prod_prod c.
 // ---------------------------------------------------------------------
 
-// Exponential of the rate expressions.  Double precision: exp().  Mixed
-// precision, where the rates are stored in float: a base-2 range reduction
+// Exponential of the rate expressions: exp(), except in the fast mixed
+// unit, where the rates are stored in float: a base-2 range reduction
 // done exactly in double (t = x log2(e) = k + f, k integer, |f| <= 1/2, in
 // the manner of Cody and Waite), 2^f from the hardware base-2 exponential
 // in float (ex2.approx, relative error about 2^-22), and 2^k added to the
 // binary exponent of the result; relative error below 5e-7.
 __device__ __forceinline__ double exp_rate(double x)
 {
-#if LBMK_MIXED
+#if LBMK_MIXED && LBMK_FAST
     const double t = x * 1.4426950408889634074;          // log2(e)
     if (!(fabs(t) < 1020.0)) return t > 0.0 ? (double)INFINITY : (t < 0.0 ? 0.0 : t);
     const double k = rint(t);
@@ -583,7 +601,7 @@ __device__ __forceinline__ double exp_rate(double x)
 // are this thread's scratch columns.
 template <int M>
 __device__ __forceinline__ void molar_production(const MechConst &mc, double T, const double *conc, double *sh_act,
-                                                 double *sh_g, Real *sh_w, int t)
+                                                 double *sh_g, WReal *sh_w, int t)
 {
     const double invT = 1.0 / T, lnT = log(T);
     const double lnTr = lnT - mc.log_T_ref;
@@ -629,7 +647,7 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
                 q *= Pr / (1.0 + Pr);
             }
         }
-        const Real qr = (Real)q;
+        const WReal qr = (WReal)q;
         for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * LBMK_BLOCK + t] -= qr;
         for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * LBMK_BLOCK + t] += qr;
     }
@@ -643,7 +661,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mas
 {
     __shared__ double sh_act[M * LBMK_BLOCK];
     __shared__ double sh_g[M * LBMK_BLOCK];
-    __shared__ Real sh_w[M * LBMK_BLOCK];
+    __shared__ WReal sh_w[M * LBMK_BLOCK];
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
@@ -760,22 +778,21 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
 
     // Eq. (tauab): 1/tau_ab = kappa / (W_a W_b D_ab), kappa = m R_U T;
     // 1/tau_a = sum_b Y_b / tau_ab.  From here to the diffusion velocities
-    // the arithmetic is in the storage type: in mixed precision these
-    // quantities are stored and used as floats, and the solve below is
-    // well conditioned (B is diagonally dominant after the symmetric
-    // scaling by Y).
+    // the arithmetic is in SReal: double, or float in the fast mixed unit
+    // (the results are stored as floats there, and the solve below is well
+    // conditioned: B is diagonally dominant after the symmetric scaling by Y).
     const double kappa = mc.r_lat * T / inv_m;
-    const Real kap = (Real)kappa, irr = (Real)ir;
-    Real Yr[M], ur[3] = {(Real)u[0], (Real)u[1], (Real)u[2]};
+    const SReal kap = (SReal)kappa, irr = (SReal)ir;
+    SReal Yr[M], ur[3] = {(SReal)u[0], (SReal)u[1], (SReal)u[2]};
 #pragma unroll
-    for (int s = 0; s < M; ++s) Yr[s] = (Real)Y[s];
-    Real ita[M];
+    for (int s = 0; s < M; ++s) Yr[s] = (SReal)Y[s];
+    SReal ita[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        Real acc = 0;
+        SReal acc = 0;
 #pragma unroll
         for (int b = 0; b < M; ++b)
-            if (b != s) acc = fma(Yr[b], INVWWD(s, b), acc);
+            if (b != s) acc = fma(Yr[b], INVWWD_S(s, b), acc);
         ita[s] = kap * acc;
     }
 
@@ -784,31 +801,31 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     //   rhs_a = Y_a (u_a - u) = j_a / rho - Y_a u.
     // B is symmetric positive definite; L D L^T without pivoting, L unit
     // lower triangular (stored below the diagonal of Ln).
-    Real du[M][3];
+    SReal du[M][3];
     {
-        Real Ln[M][M], D[M], Dinv[M];
+        SReal Ln[M][M], D[M], Dinv[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const Real hy = (Real)-0.5 * kap * Yr[i];
+            const SReal hy = (SReal)-0.5 * kap * Yr[i];
 #pragma unroll
-            for (int k = 0; k < i; ++k) Ln[i][k] = hy * INVWWD(i, k) * Yr[k];
-            Ln[i][i] = Yr[i] * fma((Real)0.5, ita[i], (Real)1);
+            for (int k = 0; k < i; ++k) Ln[i][k] = hy * INVWWD_S(i, k) * Yr[k];
+            Ln[i][i] = Yr[i] * fma((SReal)0.5, ita[i], (SReal)1);
         }
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-            Real tk[M];
+            SReal tk[M];
 #pragma unroll
             for (int j = 0; j < k; ++j) tk[j] = D[j] * Ln[k][j];
 #pragma unroll
             for (int i = k; i < M; ++i) {
-                Real sacc = Ln[i][k];
+                SReal sacc = Ln[i][k];
 #pragma unroll
                 for (int j = 0; j < k; ++j) sacc = fma(-Ln[i][j], tk[j], sacc);
                 Ln[i][k] = sacc;
             }
             D[k] = Ln[k][k];
-            if (!(D[k] > (Real)0)) flag(a.status, LBMK_BIT_PIVOT);
-            Dinv[k] = (Real)1 / D[k];
+            if (!(D[k] > (SReal)0)) flag(a.status, LBMK_BIT_PIVOT);
+            Dinv[k] = (SReal)1 / D[k];
 #pragma unroll
             for (int i = k + 1; i < M; ++i) Ln[i][k] *= Dinv[k];
         }
@@ -817,7 +834,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
         for (int i = 0; i < M; ++i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                Real sacc = fma(ja[i][d], irr, -Yr[i] * ur[d]);
+                SReal sacc = fma((SReal)ja[i][d], irr, -Yr[i] * ur[d]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) sacc = fma(-Ln[i][j], du[j][d], sacc);
                 du[i][d] = sacc;
@@ -830,7 +847,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
         for (int i = M - 1; i >= 0; --i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                Real sacc = du[i][d];
+                SReal sacc = du[i][d];
 #pragma unroll
                 for (int j = i + 1; j < M; ++j) sacc = fma(-Ln[j][i], du[j][d], sacc);
                 du[i][d] = sacc;
@@ -843,7 +860,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     const double hk = H + 0.5 * usq;
     double qeq[3], Rt[6], tr3;
     energy_moments(rho, u, P, hk, sm.rhoE, qeq, Rt, tr3);
-    Real dq[3];
+    SReal dq[3];
     {
         const double dP[6] = {sm.P[0] - (P + rho * u[0] * u[0]), sm.P[1] - (P + rho * u[1] * u[1]),
                               sm.P[2] - (P + rho * u[2] * u[2]), sm.P[3] - rho * u[0] * u[1],
@@ -851,16 +868,16 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
         const double uP[3] = {u[0] * dP[0] + u[1] * dP[3] + u[2] * dP[4],
                               u[0] * dP[3] + u[1] * dP[1] + u[2] * dP[5],
                               u[0] * dP[4] + u[1] * dP[5] + u[2] * dP[2]};
-        Real HY[M];
+        SReal HY[M];
 #pragma unroll
-        for (int s = 0; s < M; ++s) HY[s] = (Real)Ha[s] * Yr[s];
-        const Real orho = (Real)(omega1 * rho);
+        for (int s = 0; s < M; ++s) HY[s] = (SReal)Ha[s] * Yr[s];
+        const SReal orho = (SReal)(omega1 * rho);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            Real hyd = 0;
+            SReal hyd = 0;
 #pragma unroll
             for (int s = 0; s < M; ++s) hyd = fma(HY[s], du[s][d], hyd);
-            dq[d] = (Real)((omega - omega1) * (sm.q[d] - uP[d] - qeq[d])) + orho * hyd;
+            dq[d] = (SReal)((omega - omega1) * (sm.q[d] - uP[d] - qeq[d])) + orho * hyd;
         }
     }
 
@@ -889,21 +906,21 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         R[(size_t)(rr.phi + d) * N + n] = (Real)(rho * u[d] * (1.0 - 3.0 * Rm * T) - rho * u[d] * u[d] * u[d]);
-        R[(size_t)(rr.u + d) * N + n] = ur[d];
-        R[(size_t)(rr.dq + d) * N + n] = dq[d];
+        R[(size_t)(rr.u + d) * N + n] = (Real)ur[d];
+        R[(size_t)(rr.dq + d) * N + n] = (Real)dq[d];
     }
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        R[(size_t)(rr.y + s) * N + n] = Yr[s];
+        R[(size_t)(rr.y + s) * N + n] = (Real)Yr[s];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = du[s][d];
+        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = (Real)du[s][d];
         // beta_a = 1/(2 tau_a + 1), Eq. (fStar)
-        const Real it = ita[s];
-        R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
+        const SReal it = ita[s];
+        R[(size_t)(rr.beta + s) * N + n] = (Real)(it / ((SReal)2 + it));
         R[(size_t)(rr.h + s) * N + n] = (Real)Ha[s];
     }
     R[(size_t)rr.rho * N + n] = (Real)rho;
-    R[(size_t)rr.kappa * N + n] = kap;
+    R[(size_t)rr.kappa * N + n] = (Real)kap;
     R[(size_t)rr.rt * N + n] = (Real)(Rm * T);
     R[(size_t)rr.om * N + n] = (Real)omega;
     R[(size_t)rr.om1 * N + n] = (Real)omega1;
@@ -918,7 +935,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
 {
     __shared__ double sh_act[M * LBMK_BLOCK];   // c_a exp(g_a / R_U T)
     __shared__ double sh_g[M * LBMK_BLOCK];     // g_a / R_U T
-    __shared__ Real sh_w[M * LBMK_BLOCK];       // molar production
+    __shared__ WReal sh_w[M * LBMK_BLOCK];      // molar production
     const MechConst &mc = c_mech[a.slot];
     const int t = threadIdx.x;
     const int n = blockIdx.x * blockDim.x + t;
@@ -933,7 +950,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
     for (int s = 0; s < M; ++s) conc[s] = rho * (double)R[(size_t)(rr.y + s) * N + n] * mc.invW[s];
     molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, t);
 #pragma unroll
-    for (int s = 0; s < M; ++s) R[(size_t)(rr.wd + s) * N + n] = (Real)mc.W[s] * sh_w[s * LBMK_BLOCK + t];
+    for (int s = 0; s < M; ++s) R[(size_t)(rr.wd + s) * N + n] = (Real)(mc.W[s] * sh_w[s * LBMK_BLOCK + t]);
 }
 
 // ---------------------------------------------------------------------

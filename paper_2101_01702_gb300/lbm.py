@@ -33,6 +33,7 @@ LBM_BC_PERIODIC = 0
 LBM_BC_EQ_ZEROGRAD_U0LEFT = 1
 LBM_FP64 = 0
 LBM_MIXED = 1
+LBM_MIXED_FAST = 2
 LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2, 4, 8, 16, 32, 64
 LBM_F_RHO_DOT = 128
 LBM_PHASES = 5

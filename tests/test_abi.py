@@ -44,6 +44,12 @@ def test_buffer_sizes_and_validation(lib):
     assert pop == 9 * 27 * 512 * 4 + 9 * 512 * 8 + 27 * 512 * 8
     assert mac == (9 + 12) * 512 * 8 + (19 + 7 * 9) * 512 * 4
     assert gh == 0
+    lat.precision = lib.LBM_MIXED_FAST           # same layout as LBM_MIXED
+    assert lib.lbm_buffer_sizes(lat, sp) == (pop, mac, gh)
+    lat.precision = 3
+    with pytest.raises(lib.LBMError) as e:
+        lib.lbm_buffer_sizes(lat, sp)
+    assert e.value.status == lib.LBM_ERR_ARG
     lat.bc_x = 1
     lat.precision = lib.LBM_FP64
     pop, mac, gh = lib.lbm_buffer_sizes(lat, sp)

@@ -125,30 +125,40 @@ def _mixed_errors(gpu, ref, M):
     return err
 
 
-def test_mixed_sphere_against_oracle(orc, lbm):
+MIXED_MODES = ["mixed", "mixed_fast"]
+
+
+def _mode(lbm, name):
+    return {"fp64": lbm.LBM_FP64, "mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST}[name]
+
+
+@pytest.mark.parametrize("mode", MIXED_MODES)
+def test_mixed_sphere_against_oracle(orc, lbm, mode):
     prob = w.sphere3d_problem(shape=(25, 23, 21), radius=6.0)
-    s, o = _run_pair(orc, lbm, prob, 100, lbm.LBM_MIXED)
+    s, o = _run_pair(orc, lbm, prob, 100, _mode(lbm, mode))
     err = _mixed_errors(_gpu_moments(s, lbm), _oracle_moments(o), 9)
     assert max(err.values()) <= 1e-4, err
 
 
-def test_mixed_config1_against_oracle(orc, lbm):
+@pytest.mark.parametrize("mode", MIXED_MODES)
+def test_mixed_config1_against_oracle(orc, lbm, mode):
     prob = w.config1_problem()
-    s, o = _run_pair(orc, lbm, prob, 200, lbm.LBM_MIXED)
+    s, o = _run_pair(orc, lbm, prob, 200, _mode(lbm, mode))
     err = _mixed_errors(_gpu_moments(s, lbm), _oracle_moments(o), 3)
     assert max(err.values()) <= 1e-4, err
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 2e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-10), ("mixed_fast", 2e-6)])
 def test_production_rates_against_oracle(orc, lbm, precision, tol):
     """rho_dot_a (Eq. (sumRhoDot)) from lbm_moments at the GPU's own (rho_a, T)
     on a burning 1D flame, against the oracle's rate function at the same
     state, on 600 sampled nodes across the front.  Each species is
-    normalised by its largest rate.  The mixed bar covers the float
-    exponential of the rate expressions (relative error ~3e-7) and float
+    normalised by its largest rate.  Both FP64 and the mixed mode evaluate
+    the rates in double; the fast mixed bar covers its float 2^f in the
+    exponentials of the rate expressions (relative error ~3e-7) and float
     accumulation of the reaction contributions."""
     prob = w.flame1d_problem(nx=512)
-    p = lbm.LBM_FP64 if precision == "fp64" else lbm.LBM_MIXED
+    p = _mode(lbm, precision)
     s = lbm.Solver.from_problem(prob, precision=p)
     s.step(60)
     m = s.moments(lbm.LBM_F_RHO_A | lbm.LBM_F_T | lbm.LBM_F_RHO_DOT)
