@@ -353,7 +353,7 @@ def run_ours(args):
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (4 + (prob.lattice.bc_x != 0)),
+            "gpu_launches": args.steps * (5 + (prob.lattice.bc_x != 0)),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

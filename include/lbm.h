@@ -247,6 +247,14 @@ void *lbm_state_buffer(lbm_ctx *ctx);
 int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
                            const double *pop_in, double *pop_out, double *T_io, void *cuda_stream);
 
+/* Diagnostic (the paper has no counterpart): evaluates the kernels' own
+ * double-precision exponential -- the table-driven method of P. T. P. Tang
+ * (ACM Trans. Math. Softw. 15(2), 1989) used for the Arrhenius factors and
+ * equilibrium constants -- into y and the CUDA math library's exp into
+ * y_ref, for n arguments x.  x, y, y_ref: device, double [n].  Waits for
+ * the stream; LBM_ERR_ARG for NULL pointers or n < 0. */
+int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream);
+
 /* Frees host state and the status word; never the caller's buffers. */
 int lbm_destroy(lbm_ctx *ctx);
 

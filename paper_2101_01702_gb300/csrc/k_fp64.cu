@@ -1,6 +1,27 @@
 // Kernels of the reactive-mixture lattice Boltzmann step, double-precision populations.
 #define LBMK_MIXED 0
+#include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
+
+namespace {
+__global__ void k_exp_check(const double *x, double *y, double *y_ref, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    y[i] = exp_table(x[i]);
+    y_ref[i] = exp(x[i]);
+}
+}  // namespace
+
+extern "C" int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream)
+{
+    if (!x || !y || !y_ref || n < 0) return LBM_ERR_ARG;
+    if (n == 0) return LBM_OK;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    k_exp_check<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, y_ref, n);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
 
 namespace lbmk {
 

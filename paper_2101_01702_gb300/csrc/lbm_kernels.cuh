@@ -10,7 +10,7 @@
 // the Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
 // their equilibrium constants are double precision.
 //
-// One time step is five launches on one stream:
+// One time step is six launches on one stream:
 //   k_ghost  x-face ghost nodes (Sec. 5a; only for non-periodic x)
 //   k_pre    pull, all moments, Newton temperature, relaxation rates,
 //            Stefan-Maxwell diffusion velocities, the local part of the
@@ -18,9 +18,11 @@
 //            writes the per-node record.
 //   k_chem   production rates of the reaction mechanism (record rows)
 //   k_grad   G_alpha = (1/omega - 1/2) d_alpha Phi_alpha (Eq. (Xalpha))
-//   k_step   pull again, X = -d_alpha G_alpha and sum_a H_a grad Y_a from the
-//            neighbours' records, and the collisions of
-//            Eqs. (finalNumericalEquations), (f), (g), direction by direction
+//   k_step_g pull of the energy set, sum_a H_a grad Y_a from the neighbours'
+//            records, and the collision of Eq. (g) (double)
+//   k_step   pull of the species and mixture sets, X = -d_alpha G_alpha from
+//            the neighbours' records, and the collisions of
+//            Eqs. (finalNumericalEquations), (f), direction by direction
 // One thread owns one lattice node; populations are structure-of-arrays
 // [set][direction][node] so that a warp's pulls are coalesced rows.
 #pragma once
@@ -56,14 +58,17 @@ typedef double WReal;
 #define LBMK_BLOCK 128
 // Minimum resident blocks per SM asked of the compiler for the two large
 // kernels (register budget 65536 / (LBMK_BLOCK * minB)).  Measured on the
-// 256^3 nine-species lattice: the moment pass is latency bound and runs
-// fastest at 5 blocks (mixed; 96 registers, some spilled) and 3 blocks
-// (double; 168 registers); the collision pass runs fastest unconstrained.
+// 256^3 nine-species lattice: the moment pass runs fastest at 5 blocks in
+// the fast mixed unit (96 registers, some spilled; latency bound) and at 3
+// in the double unit; with its double Stefan-Maxwell solve the mixed unit
+// is FP64-bound and insensitive to it (2..5 within 1 %).  The species and
+// mixture collision runs fastest at 3 blocks in the mixed units (168
+// registers) and unconstrained in the double unit.
 #ifndef LBMK_PRE_MINB
 #define LBMK_PRE_MINB (LBMK_MIXED ? 5 : 3)
 #endif
 #ifndef LBMK_STEP_MINB
-#define LBMK_STEP_MINB 1
+#define LBMK_STEP_MINB (LBMK_MIXED ? 3 : 1)
 #endif
 #if LBMK_MIXED
 #define INVWWD(a_, b_) (mc.inv_WWD_f[a_][b_])
@@ -575,7 +580,52 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
 // which equals k_f prod_reac c - (k_f / K_c) prod_prod c.
 // ---------------------------------------------------------------------
 
-// Exponential of the rate expressions: exp(), except in the fast mixed
+// 2^(j/64), j = 0..63, each the double nearest to the exact value (60-digit
+// evaluation of 2^(j/64), rounded once).
+__device__ const double c_exp2_64[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
+};
+
+// exp(x) by the table-driven method of P. T. P. Tang (ACM Trans. Math.
+// Softw. 15(2), 1989): x = (64 m + j) ln2/64 + r with |r| <= ln2/128, so
+// exp(x) = 2^m 2^(j/64) e^r, and e^r - 1 is its degree-5 Taylor polynomial
+// (truncation error below 4e-17).  ln2/64 = L1 + L2 with L1 rounded to 36
+// significant bits, so that N L1 is exact for |N| < 2^17 and the reduced
+// argument carries no cancellation error (Cody and Waite).  N = rint(x 64/ln2)
+// by the 1.5 2^52 rounding constant; 2^m is added to the result's binary
+// exponent.  |x| >= 707 (where 2^m leaves the normal range) goes to exp().
+// About 1 ulp; 11 double operations.
+__device__ __forceinline__ double exp_table(double x)
+{
+    if (!(fabs(x) < 707.0)) return exp(x);
+    const double kRound = 6755399441055744.0;                 // 1.5 * 2^52
+    const double t = fma(x, 0x1.71547652b82fep+6, kRound);    // x 64/ln2, rounded to an integer
+    const int n = __double2loint(t);
+    const double N = t - kRound;
+    double r = fma(-N, 0x1.62e42fefa0000p-7, x);              // L1
+    r = fma(-N, 0x1.cf79abc9e3b3ap-46, r);                    // L2
+    const double p = fma(fma(fma(fma(1.0 / 120.0, r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5), r * r, r);
+    const double Tj = __ldg(&c_exp2_64[n & 63]);
+    const double y = fma(Tj, p, Tj);
+    return __hiloint2double(__double2hiint(y) + (n >> 6) * (1 << 20), __double2loint(y));
+}
+
+// Exponential of the rate expressions: exp_table(), except in the fast mixed
 // unit, where the rates are stored in float: a base-2 range reduction
 // done exactly in double (t = x log2(e) = k + f, k integer, |f| <= 1/2, in
 // the manner of Cody and Waite), 2^f from the hardware base-2 exponential
@@ -592,7 +642,7 @@ __device__ __forceinline__ double exp_rate(double x)
     const double r = (double)y;                          // in [2^-1/2, 2^1/2]
     return __hiloint2double(__double2hiint(r) + (int)k * (1 << 20), __double2loint(r));
 #else
-    return exp(x);
+    return exp_table(x);
 #endif
 }
 
@@ -617,18 +667,19 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
     }
     const double c0 = mc.P0_over_r * invT, ic0 = T / mc.P0_over_r;   // P0/(r T) and its inverse
     for (int k = 0; k < mc.R; ++k) {
-        double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k]));
-        const int nr = mc.nreac[k], np = mc.nprod[k];
-        double pf = 1.0;
-        for (int j = 0; j < nr; ++j) {
+        const int nr = mc.nreac[k], np = mc.nprod[k];     // nr >= 1 (checked at packing)
+        const int s0 = mc.reac[k][0] * LBMK_BLOCK + t;
+        double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k])) - sh_g[s0];
+        double pf = sh_act[s0];
+        for (int j = 1; j < nr; ++j) {
             const int sidx = mc.reac[k][j] * LBMK_BLOCK + t;
             arg -= sh_g[sidx];
             pf *= sh_act[sidx];
         }
         double q = pf;
         if (mc.rev[k]) {
-            double pr = 1.0;
-            for (int j = 0; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
+            double pr = np > 0 ? sh_act[mc.prod[k][0] * LBMK_BLOCK + t] : 1.0;
+            for (int j = 1; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
             const int dn = mc.dn[k];
             for (int j = 0; j < dn; ++j) pr *= ic0;
             for (int j = 0; j < -dn; ++j) pr *= c0;
@@ -983,12 +1034,109 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
 }
 
 // ---------------------------------------------------------------------
-// Pass 3: the collisions, direction by direction.
+// Pass 3a: collision of the energy set g, Eq. (g) in the regularised form
+//   g + omega (g^eq - g) + w_i (Dq . c_i) / theta,
+// with the grad-Y part of Dq (Eq. (corrFourier)) from the neighbours'
+// records.  The post-collision value is (1 - omega) g_i + B_i with
+//   B_i = omega g_i^eq + 3 w_i c_i . Dq
+//       = w_i [A0 + c_i . A1 + sum_d c_id^2 A2_d + sum_{d<e} c_id c_ie A3_de],
+//   A0 = omega (rho E - (9/2) tr3),  A1 = 3 (omega q^eq + Dq),
+//   A2_d = (9/2) omega R_dd,         A3_de = 9 omega R_de,
+// R = R^eq - rho E theta I (Eq. (gieq) expanded in c_i).  Double precision.
+// ---------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_step_g(StepArgs a)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const int n = nd.n;
+    const size_t N = a.N;
+    const RecRows rr = rec_rows(M);
+    const Real *R = rec(a);
+    auto ld = [&](int row) { return R[(size_t)row * N + n]; };
+    auto ldd = [&](int row) { return a.macro[(size_t)row * N + n]; };
+
+    // sum_a H_a grad Y_a (Eq. (corrFourier)), H_a of this node
+    Real Hl[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) Hl[s] = ld(rr.h + s);
+    Real HgY[3] = {0, 0, 0};
+    {
+        StencilIdx st;
+        make_stencil(st, nd, a);
+        const Real *Yf = R + (size_t)rr.y * N;
+        for_dirs<0, LBMK_Q>([&](auto dd) {
+            constexpr int I = decltype(dd)::value;
+            if constexpr (I != REST) {
+                const size_t nb = nb_of<I>(st);
+                Real hy = 0;
+#pragma unroll
+                for (int s = 0; s < M; ++s) hy += Hl[s] * Yf[s * N + nb];
+                constexpr Real wx = (Real)(WI(I) * CX(I)), wy = (Real)(WI(I) * CY(I)), wz = (Real)(WI(I) * CZ(I));
+                if (CX(I)) HgY[0] += wx * hy;
+                if (CY(I)) HgY[1] += wy * hy;
+                if (CZ(I)) HgY[2] += wz * hy;
+            }
+        });
+    }
+    const Real om1 = ld(rr.om1), P = ld(rr.p);
+    const double omd = (double)ld(rr.om), om1m = 1.0 - omd;
+    double gD[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gD[d] = (double)(ld(rr.dq + d) + (Real)1.5 * ((Real)2 - om1) * P * HgY[d]);
+    // energy equilibrium moments (Eqs. (geq1mom), (geq2mom))
+    const double gE = ldd(dr_ge(M));
+    double gq[3], gR[6];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) gq[d] = ldd(dr_gq(M) + d);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) gR[d] = ldd(dr_gr(M) + d);
+    const double gtr = ldd(dr_gtr(M));
+    const double A0 = omd * (gE - 4.5 * gtr);
+    double A1[3], A2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        A1[d] = 3.0 * fma(omd, gq[d], gD[d]);
+        A2[d] = 4.5 * omd * gR[d];
+    }
+    const double A3xy = 9.0 * omd * gR[3], A3xz = 9.0 * omd * gR[4], A3yz = 9.0 * omd * gR[5];
+
+    const PopView v = view(a.src, a);
+    PullIdx p;
+    make_pull(p, nd, a);
+    double gcheck = 0.0;
+    // row by row: j = (cy+1) + 3 (cz+1), then cx = -1, 0, 1 (i = (cx+1) + 3 j)
+    for_dirs<0, 9>([&](auto dj) {
+        constexpr int j = decltype(dj)::value, cy = j % 3 - 1, cz = j / 3 - 1;
+        constexpr int nnz = (cy != 0) + (cz != 0);
+        double base = A0, lin = A1[0];
+        if (cy) { base += cy * A1[1] + A2[1]; lin += cy * A3xy; }
+        if (cz) { base += cz * A1[2] + A2[2]; lin += cz * A3xz; }
+        if (cy && cz) base += (cy * cz) * A3yz;
+        // w_i = w(cx) w(cy) w(cz) with w(0) = 2/3, w(+-1) = 1/6
+        constexpr double w0 = nnz == 0 ? 8.0 / 27.0 : (nnz == 1 ? 2.0 / 27.0 : 1.0 / 54.0);
+        constexpr double w1 = nnz == 0 ? 2.0 / 27.0 : (nnz == 1 ? 1.0 / 54.0 : 1.0 / 216.0);
+        const double bq = base + A2[0];
+        const double B[3] = {w1 * (bq - lin), w0 * base, w1 * (bq + lin)};
+        for_dirs<0, 3>([&](auto dx) {
+            constexpr int k = decltype(dx)::value, I = k + 3 * j;
+            const double val = fma(om1m, pull_g(v, a, I, p), B[k]);
+            store_g(a.dst, a, I, n, val);
+            gcheck += val;
+        });
+    });
+    if (!isfinite(gcheck)) flag(a.status, LBMK_BIT_NONFINITE);
+}
+
+// ---------------------------------------------------------------------
+// Pass 3b: collisions of the species sets (Eq. (finalNumericalEquations)
+// with the quasi-equilibria of Eq. (fStar)) and of the mixture set f
+// (Eq. (f) with the isotropy correction of Eq. (Ai)), direction by
+// direction, in the storage precision.
 // ---------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 {
-    __shared__ double sh_B[LBMK_Q * LBMK_BLOCK];   // B_i of the energy-set collision
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
@@ -999,47 +1147,30 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
     auto ld = [&](int row) { return R[(size_t)row * N + n]; };
     auto ldd = [&](int row) { return a.macro[(size_t)row * N + n]; };
 
-    // X = -d_alpha G_alpha (Eq. (Xalpha)) and sum_a H_a grad Y_a (Eq. (corrFourier))
-    Real Hl[M];
-#pragma unroll
-    for (int s = 0; s < M; ++s) Hl[s] = ld(rr.h + s);
-    Real X[3] = {0, 0, 0}, HgY[3] = {0, 0, 0};
+    // X = -d_alpha G_alpha (Eq. (Xalpha))
+    Real X[3] = {0, 0, 0};
     {
         StencilIdx st;
         make_stencil(st, nd, a);
         const Real *G = R + (size_t)rr.g * N;
-        const Real *Yf = R + (size_t)rr.y * N;
         for_dirs<0, LBMK_Q>([&](auto dd) {
             constexpr int I = decltype(dd)::value;
             if constexpr (I != REST) {
                 const size_t nb = nb_of<I>(st);
-                Real hy = 0;
-#pragma unroll
-                for (int s = 0; s < M; ++s) hy += Hl[s] * Yf[s * N + nb];
                 constexpr Real wx = (Real)(WI(I) * CX(I)), wy = (Real)(WI(I) * CY(I)), wz = (Real)(WI(I) * CZ(I));
-                if (CX(I)) { X[0] += wx * G[nb]; HgY[0] += wx * hy; }
-                if (CY(I)) { X[1] += wy * G[N + nb]; HgY[1] += wy * hy; }
-                if (CZ(I)) { X[2] += wz * G[2 * N + nb]; HgY[2] += wz * hy; }
+                if (CX(I)) X[0] += wx * G[nb];
+                if (CY(I)) X[1] += wy * G[N + nb];
+                if (CZ(I)) X[2] += wz * G[2 * N + nb];
             }
         });
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { X[k] *= (Real)-3; HgY[k] *= (Real)3; }
+        for (int k = 0; k < 3; ++k) X[k] *= (Real)-3;
     }
 
-    const Real rho = ld(rr.rho), om = ld(rr.om), om1 = ld(rr.om1), P = ld(rr.p);
+    const Real rho = ld(rr.rho), om = ld(rr.om);
     const Real kappa = ld(rr.kappa), RT = ld(rr.rt);
     const Real u[3] = {ld(rr.u), ld(rr.u + 1), ld(rr.u + 2)};
     const Real T = (Real)ldd(DR_T);
-    Real gD[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) gD[d] = ld(rr.dq + d) + (Real)0.5 * ((Real)2 - om1) * P * HgY[d];
-    // energy equilibrium moments in double (Eqs. (geq1mom), (geq2mom))
-    const double gE = ldd(dr_ge(M));
-    const double gq[3] = {ldd(dr_gq(M)), ldd(dr_gq(M) + 1), ldd(dr_gq(M) + 2)};
-    double gR[6];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) gR[d] = ldd(dr_gr(M) + d);
-    const double gtr = ldd(dr_gtr(M));
 
     // per-species data: mass fraction, quasi-equilibrium velocity u + du_b,
     // beta_b and rho_dot_b (densities, zeta and the products are formed per
@@ -1055,61 +1186,25 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
     }
     const Real u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
 
-    // Energy set, Eq. (g) in the regularised form: the post-collision value
-    // is (1 - omega) g_i + B_i with
-    //   B_i = omega g_i^eq + 3 w_i c_i . Dq
-    //       = w_i [A0 + c_i . A1 + sum_d c_id^2 A2_d + sum_{d<e} c_id c_ie A3_de],
-    //   A0 = omega (rho E - (9/2) tr3),  A1 = 3 (omega q^eq + Dq),
-    //   A2_d = (9/2) omega R_dd,         A3_de = 9 omega R_de,
-    // R = R^eq - rho E theta I (Eq. (gieq) expanded in c_i).
-    const double omd = (double)om, om1m = 1.0 - omd;
-    const double A0 = omd * (gE - 4.5 * gtr);
-    double A1[3], A2[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        A1[d] = 3.0 * fma(omd, gq[d], (double)gD[d]);
-        A2[d] = 4.5 * omd * gR[d];
-    }
-    const double A3xy = 9.0 * omd * gR[3], A3xz = 9.0 * omd * gR[4], A3yz = 9.0 * omd * gR[5];
-    // B_i of the 27 directions, kept in this thread's column of shared memory
-    for_dirs<0, 9>([&](auto dj) {
-        constexpr int j = decltype(dj)::value, cy = j % 3 - 1, cz = j / 3 - 1;
-        constexpr int nnz = (cy != 0) + (cz != 0);
-        double base = A0, lin = A1[0];
-        if (cy) { base += cy * A1[1] + A2[1]; lin += cy * A3xy; }
-        if (cz) { base += cz * A1[2] + A2[2]; lin += cz * A3xz; }
-        if (cy && cz) base += (cy * cz) * A3yz;
-        // w_i = w(cx) w(cy) w(cz) with w(0) = 2/3, w(+-1) = 1/6
-        constexpr double w0 = nnz == 0 ? 8.0 / 27.0 : (nnz == 1 ? 2.0 / 27.0 : 1.0 / 54.0);
-        constexpr double w1 = nnz == 0 ? 2.0 / 27.0 : (nnz == 1 ? 1.0 / 54.0 : 1.0 / 216.0);
-        const double bq = base + A2[0];
-        sh_B[(3 * j) * LBMK_BLOCK + threadIdx.x] = w1 * (bq - lin);
-        sh_B[(3 * j + 1) * LBMK_BLOCK + threadIdx.x] = w0 * base;
-        sh_B[(3 * j + 2) * LBMK_BLOCK + threadIdx.x] = w1 * (bq + lin);
-    });
-
     const PopView v = view(a.src, a);
     PullIdx p;
     make_pull(p, nd, a);
     Real check = 0;
-    double gcheck = 0.0;
 
     // Directions row by row: j = (cy+1) + 3 (cz+1), then cx = -1, 0, 1
     // (direction i = (cx+1) + 3 j, i.e. i = 0..26 in order).  The y-z
-    // factors of the product-form equilibria are formed once per row.  In mixed precision the populations of direction
-    // i+1 are loaded while direction i is collided (raw stored values; the
-    // rest state is added where they are used).
+    // factors of the product-form equilibria are formed once per row.  In
+    // mixed precision the populations of direction i+1 are loaded while
+    // direction i is collided (raw stored values; the rest state is added
+    // where they are used).
     constexpr bool kPrefetch = LBMK_MIXED;
     Real fraw[M];
-    double graw = 0.0;
     auto load_raw = [&](int i) {
         const Src sr = src_of(i, p, a);
         if (sr.ghost) {
-            graw = load_ghost(a, sr.side, M, i, sr.idx);
 #pragma unroll
             for (int s = 0; s < M; ++s) fraw[s] = (Real)load_ghost(a, sr.side, s, i, sr.idx) - RAWREF(s, i);
         } else {
-            graw = load_g(v, i, sr.idx);
             if (LBMK_MIXED && i == REST) return;
 #pragma unroll
             for (int s = 0; s < M; ++s) fraw[s] = load_raw_sf(v, s, i, sr.idx);
@@ -1141,22 +1236,14 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
             AXyz = nnz == 1 ? (Real)0.5 * ((Real)cy * X[1] + (Real)cz * X[2]) : (Real)0;
         }
         Real fc[M];
-        double gc;
         if (kPrefetch) {
 #pragma unroll
             for (int s = 0; s < M; ++s) fc[s] = fraw[s];
-            gc = graw;
             if (i + 1 < LBMK_Q) load_raw(i + 1);
         } else {
             load_raw(i);
 #pragma unroll
             for (int s = 0; s < M; ++s) fc[s] = fraw[s];
-            gc = graw;
-        }
-        {
-            const double val = fma(om1m, gc, sh_B[i * LBMK_BLOCK + threadIdx.x]);
-            store_g(a.dst, a, i, n, val);
-            gcheck += val;
         }
         if (LBMK_MIXED && i == REST) continue;   // rest of the species and mixture sets: below
         Real eqp[M], Dl[M];
@@ -1230,7 +1317,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
         check += (Real)val;
     }
 #endif
-    if (!isfinite(check) || !isfinite(gcheck)) flag(a.status, LBMK_BIT_NONFINITE);
+    if (!isfinite(check)) flag(a.status, LBMK_BIT_NONFINITE);
 }
 
 // ---------------------------------------------------------------------
@@ -1253,6 +1340,7 @@ int run_step(const StepArgs &a, cudaEvent_t *ev)
     if (ev) cudaEventRecord(ev[3], a.stream);
     k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[4], a.stream);
+    k_step_g<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[5], a.stream);
     return (int)cudaGetLastError();

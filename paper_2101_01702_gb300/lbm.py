@@ -87,7 +87,7 @@ _lib.lbm_strerror.restype = C.c_char_p
 
 EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
-            "lbm_strerror", "lbm_step_fixed_scratch"]
+            "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check"]
 
 
 def library_path() -> str:
@@ -163,6 +163,16 @@ def lbm_state_buffer(ctx) -> int:
 
 def lbm_destroy(ctx) -> int:
     return _lib.lbm_destroy(ctx)
+
+
+_lib.lbm_exp_check.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+_lib.lbm_exp_check.restype = C.c_int
+
+
+def lbm_exp_check(x_ptr: int, y_ptr: int, y_ref_ptr: int, n: int, stream: int) -> int:
+    """The kernels' exponential into y and CUDA's exp into y_ref (device)."""
+    return _lib.lbm_exp_check(C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(y_ref_ptr), int(n),
+                              C.c_void_p(stream))
 
 
 def lbm_step_fixed_scratch(lat, sp, mech, pop_in_ptr: int, pop_out_ptr: int, T_io_ptr: int, stream: int) -> int:
