@@ -361,6 +361,81 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_flames(args):
+    """The batched quasi-1D flames: 48 ragged flames side by side in one
+    lattice, stepped with one set of launches per step (plain and through a
+    captured CUDA graph), against the same 48 flames stepped one flame at a
+    time (one context per flame, sharing the batch's tables)."""
+    import torch
+    import workload as w
+    from paper_2101_01702_gb300 import build
+    build.build()
+    from paper_2101_01702_gb300 import lbm
+
+    modes = {"mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST, "fp64": lbm.LBM_FP64}
+    precision = modes[args.precision]
+    prob = w.batched_flames_problem()
+    N = prob.lattice.n_nodes
+    K = args.steps
+    stream = torch.cuda.Stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    batch = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
+    batch.step(args.warmup)
+    with ClockSampler(0) as clk:
+        ms_plain = timed(lambda: batch.step_async(K))
+        batch.step_graph(2)                       # capture outside the timed region
+        assert batch.sync() == lbm.LBM_OK
+        ms_graph = timed(lambda: batch.step_graph(K))
+    assert batch.sync() == lbm.LBM_OK
+    refs = batch.references() if precision != lbm.LBM_FP64 else None
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+
+    flames = []
+    for k in range(len(prob.lattice.seg_nx)):
+        fk = w.flame_of_batch(prob, k)
+        s = lbm.Solver.from_problem(fk, precision=precision, stream=stream, init=False)
+        if refs is not None:
+            s.set_references(refs)
+        s.init(fk.init.X, fk.init.T, fk.init.u, fk.init.P)
+        s.step(args.warmup)
+        flames.append(s)
+
+    def loop():
+        for _ in range(K):
+            for s in flames:
+                s.step_async(1)
+    ms_loop = timed(loop)
+    for s in flames:
+        assert s.sync() == lbm.LBM_OK
+        s.close()
+
+    mlups = lambda ms: N * K / (ms * 1e-3) / 1e6
+    line = {"metric": "MLUPS (batched quasi-1D flames, one launch set per step)", "value": mlups(ms_graph),
+            "unit": "MLUPS", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms_graph / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if precision != lbm.LBM_FP64 else "f64", "data": "synthetic",
+            "config": {"workload": f"flames{len(prob.lattice.seg_nx)}_M9_{args.precision}", "nodes": N,
+                       "flames": len(prob.lattice.seg_nx), "lengths": [min(prob.lattice.seg_nx),
+                                                                         max(prob.lattice.seg_nx)],
+                       "cross_section": "4x4"},
+            "batched_graph_mlups": mlups(ms_graph), "batched_plain_mlups": mlups(ms_plain),
+            "loop_single_flames_mlups": mlups(ms_loop), "speedup_vs_loop": ms_loop / ms_graph,
+            "gpu_launches": K * 6,      # ghost, moments, rates, gradients, energy and species collisions
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,11 +448,14 @@ def main():
     ap.add_argument("--skip-fast", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "flames48":
+        run_flames(args)
     else:
         run_ours(args)
 

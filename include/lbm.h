@@ -76,6 +76,16 @@ typedef struct {
     int nx, ny, nz;
     int bc_x;
     int precision;
+    /* Batches of independent lattices (the paper's 1D flame setup of Sec. 5a
+     * repeated): nseg >= 2 places nseg lattices of seg_nx[k] x ny x nz
+     * nodes side by side along x (sum of seg_nx = nx; bc_x must be
+     * LBM_BC_EQ_ZEROGRAD_U0LEFT).  Each has its own ghost nodes on both x
+     * faces, and no population, gradient stencil or ghost crosses from one
+     * to the next: every lattice evolves exactly as it would alone.
+     * nseg = 0 or 1: one lattice (seg_nx unused).  seg_nx is read during
+     * lbm_buffer_sizes and lbm_create only. */
+    int nseg;
+    const int *seg_nx;
 } lbm_lattice;
 
 /* Species, thermodynamics and transport (paper Secs. 2-3).
@@ -146,8 +156,9 @@ typedef struct {
  *                 storage type (float in the mixed modes): moments,
  *                 relaxation rates, diffusion velocities, production rates
  *                 and the inputs of the gradient stencils.
- *   ghost         x-face ghost populations, double [2][M+1][27][ny*nz];
- *                 may be NULL for periodic x. */
+ *   ghost         x-face ghost populations, double [2 G][M+1][27][ny*nz]
+ *                 with G = max(nseg, 1) lattices (left then right face of
+ *                 each); may be NULL for periodic x. */
 typedef struct {
     void *pop_a, *pop_b, *macro, *ghost;
     size_t pop_bytes, macro_bytes, ghost_bytes;
@@ -175,6 +186,15 @@ int lbm_step(lbm_ctx *ctx, int n);
 
 /* Enqueues n time steps without waiting; errors surface at lbm_sync(). */
 int lbm_step_async(lbm_ctx *ctx, int n);
+
+/* lbm_step_async through a CUDA graph.  The first call captures two time
+ * steps (A -> B -> A) on the context's stream and instantiates the graph;
+ * each call then launches it n/2 times, plus one ordinary step when n is
+ * odd or the current state is not in the graph's starting buffer.  Cuts
+ * the per-step launch cost of small lattices and batches; the results are
+ * those of lbm_step_async.  The stream must not be the legacy default
+ * stream (LBM_ERR_UNSUPPORTED).  Errors surface at lbm_sync(). */
+int lbm_step_graph(lbm_ctx *ctx, int n);
 
 /* lbm_step_async with CUDA events recorded on the stream between the
  * kernels of each step (all steps enqueued back to back, one wait at the
@@ -211,8 +231,23 @@ size_t lbm_moments_count(const lbm_ctx *ctx, unsigned mask);
 int lbm_get_populations(lbm_ctx *ctx, double *host_out);
 
 /* Device pointer of the buffer that holds the current state (pop_a or
- * pop_b); with the T row of macro it is everything a checkpoint needs. */
+ * pop_b); with the T row of macro (and, in the mixed modes, the rest
+ * references below) it is everything a checkpoint needs. */
 void *lbm_state_buffer(lbm_ctx *ctx);
+
+/* Mixed modes: the rest references the stored float deviations are taken
+ * from, float [M][27] (set s = 0..M-1, direction i; the rest direction 13
+ * is unused and reads 0).  lbm_init chooses them from the initial fields
+ * (each set's rest equilibrium at its smallest initial density and the
+ * mean initial temperature); lbm_set_references fixes them instead, so
+ * that a later lbm_init keeps them -- for restarting from a checkpoint
+ * written with those references, or for giving several contexts the same
+ * tables (contexts with identical mechanism and references share one
+ * constant-memory slot; each precision has 4 slots).  Set before lbm_init
+ * or before restoring a state.  LBM_ERR_UNSUPPORTED for LBM_FP64,
+ * LBM_ERR_ARG for NULL or non-finite values. */
+int lbm_get_references(const lbm_ctx *ctx, float *ref);
+int lbm_set_references(lbm_ctx *ctx, const float *ref);
 
 /* One double-precision time step that allocates nothing (the paper has no
  * counterpart; this is a service for callers).  Some callers cannot call

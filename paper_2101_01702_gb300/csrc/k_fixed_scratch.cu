@@ -61,6 +61,7 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     if (!lat || !sp || !mech || !pop_in || !pop_out || !T_io || pop_in == pop_out) return LBM_ERR_ARG;
     if (lat->precision != LBM_FP64) return LBM_ERR_UNSUPPORTED;
     if (lat->bc_x != LBM_BC_PERIODIC && lat->bc_x != LBM_BC_EQ_ZEROGRAD_U0LEFT) return LBM_ERR_ARG;
+    if (lat->nseg > 1) return LBM_ERR_UNSUPPORTED;   // batches of lattices: lbm_create
     if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || sp->M < 2 || sp->M > LBMK_MAXM) return LBM_ERR_ARG;
     if (sp->M != 2 && sp->M != 3 && sp->M != 9) return LBM_ERR_UNSUPPORTED;
     const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
@@ -86,6 +87,9 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     a.nz = lat->nz;
     a.N = (int)N;
     a.bc_x = lat->bc_x;
+    a.nseg = 0;
+    a.xseg = nullptr;
+    a.segs = nullptr;
     a.src = pop_in;
     a.dst = pop_out;
     a.status = (unsigned *)scratch;

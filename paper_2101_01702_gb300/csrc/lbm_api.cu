@@ -25,12 +25,26 @@ struct lbm_ctx {
     size_t pop_bytes;
     unsigned *status;        // device status word
     MechConst mc;            // host copy of the constant-memory record
+    int nseg;                // lattices side by side in x (>= 2), else 0
+    int4 *xseg;              // device [nx]: {x0, x1, k, 0} of the lattice at x
+    int2 *segs;              // device [nseg]: {x0, x1} of lattice k
+    cudaGraphExec_t graph;   // two captured steps (lbm_step_graph), or null
+    int graph_cur;           // value of cur the graph starts from
+    bool refs_fixed;         // rest references set by lbm_set_references
 };
 
 namespace {
 
+// Constant-memory slots of each kernel unit (precision).  Contexts whose
+// packed tables are identical -- the same mechanism and, in the mixed
+// modes, the same rest references -- share a slot; a slot is uploaded when
+// it is taken and reused once no context refers to it.
+struct SlotTable {
+    int refs[LBMK_SLOTS];
+    MechConst mc[LBMK_SLOTS];
+};
 std::mutex g_slot_mutex;
-bool g_slot_used[LBMK_SLOTS] = {false, false, false, false};
+SlotTable g_slots[3];
 
 bool supported_M(int M) { return M == 2 || M == 3 || M == 9; }
 
@@ -45,6 +59,56 @@ const lbmk::PrecisionOps kOps[3] = {
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
+// A slot of precision p holding mc (shared or newly uploaded on stream and
+// waited for); -1 when every slot holds other tables.
+int acquire_slot(int p, const MechConst &mc, cudaStream_t stream, int *err)
+{
+    *err = LBM_OK;
+    std::lock_guard<std::mutex> lk(g_slot_mutex);
+    SlotTable &t = g_slots[p];
+    for (int s = 0; s < LBMK_SLOTS; ++s)
+        if (t.refs[s] > 0 && memcmp(&t.mc[s], &mc, sizeof(MechConst)) == 0) {
+            ++t.refs[s];
+            return s;
+        }
+    for (int s = 0; s < LBMK_SLOTS; ++s)
+        if (t.refs[s] == 0) {
+            if (ops(p).upload(s, mc, stream) != 0 || cudaStreamSynchronize(stream) != cudaSuccess) {
+                *err = LBM_ERR_CUDA;
+                return -1;
+            }
+            t.mc[s] = mc;
+            t.refs[s] = 1;
+            return s;
+        }
+    *err = LBM_ERR_UNSUPPORTED;
+    return -1;
+}
+
+void release_slot(int p, int s)
+{
+    if (s < 0 || s >= LBMK_SLOTS) return;
+    std::lock_guard<std::mutex> lk(g_slot_mutex);
+    if (g_slots[p].refs[s] > 0) --g_slots[p].refs[s];
+}
+
+// Moves context c to a slot holding c->mc (after its stream has drained,
+// so that none of its kernels still reads the old slot).
+int reslot(lbm_ctx *c)
+{
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    int err;
+    const int s = acquire_slot(c->lat.precision, c->mc, c->stream, &err);
+    if (s < 0) return err;
+    release_slot(c->lat.precision, c->slot);
+    c->slot = s;
+    if (c->graph) {                      // captured with the old slot
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LBM_OK;
+}
+
 int map_status(unsigned bits)
 {
     if (bits & LBMK_BIT_NONFINITE) return LBM_ERR_NONFINITE;
@@ -52,6 +116,21 @@ int map_status(unsigned bits)
     if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
     if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
     return LBM_OK;
+}
+
+// Lattices side by side in x: LBM_OK when lat describes one lattice or a
+// valid batch (lengths >= 1 summing to nx, equilibrium ghost faces).
+int check_segments(const lbm_lattice *lat)
+{
+    if (lat->nseg < 0) return LBM_ERR_ARG;
+    if (lat->nseg <= 1) return LBM_OK;
+    if (!lat->seg_nx || lat->bc_x != LBM_BC_EQ_ZEROGRAD_U0LEFT || lat->nseg > lat->nx) return LBM_ERR_ARG;
+    long long sum = 0;
+    for (int k = 0; k < lat->nseg; ++k) {
+        if (lat->seg_nx[k] < 1) return LBM_ERR_ARG;
+        sum += lat->seg_nx[k];
+    }
+    return sum == lat->nx ? LBM_OK : LBM_ERR_ARG;
 }
 
 bool is_device_ptr(const void *p)
@@ -75,6 +154,9 @@ StepArgs args_of(const lbm_ctx *c)
     a.nz = c->lat.nz;
     a.N = c->N;
     a.bc_x = c->lat.bc_x;
+    a.nseg = c->nseg;
+    a.xseg = c->xseg;
+    a.segs = c->segs;
     a.src = c->buf[c->cur];
     a.dst = c->buf[1 - c->cur];
     a.macro = c->macro;
@@ -135,12 +217,17 @@ int lbm_buffer_sizes(const lbm_lattice *lat, const lbm_species *sp, size_t *pop_
     if (!lat || !sp || lat->nx < 1 || lat->ny < 1 || lat->nz < 1 || sp->M < 2 || sp->M > LBMK_MAXM)
         return LBM_ERR_ARG;
     if (!valid_precision(lat->precision)) return LBM_ERR_ARG;
+    if (lat->bc_x != LBM_BC_PERIODIC && lat->bc_x != LBM_BC_EQ_ZEROGRAD_U0LEFT) return LBM_ERR_ARG;
+    if (check_segments(lat) != LBM_OK) return LBM_ERR_ARG;
     const size_t N = (size_t)lat->nx * lat->ny * lat->nz;
     const size_t S = (size_t)sp->M + 1;
     const size_t st = store_size(lat->precision);
     if (pop_bytes) *pop_bytes = pop_bytes_for((int)S, N, is_mixed(lat->precision));
     if (macro_bytes) *macro_bytes = macro_bytes_for(sp->M, N, st);
-    if (ghost_bytes) *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : ghost_bytes_for((int)S, (size_t)lat->ny * lat->nz);
+    if (ghost_bytes)
+        *ghost_bytes = lat->bc_x == LBM_BC_PERIODIC
+                           ? 0
+                           : ghost_bytes_for((int)S, (size_t)lat->ny * lat->nz, lat->nseg > 1 ? lat->nseg : 1);
     return LBM_OK;
 }
 
@@ -167,18 +254,13 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     r = lbm_pack_tables(sp, mech, mc);
     if (r != LBM_OK) return r;
 
-    int slot = -1;
-    {
-        std::lock_guard<std::mutex> lk(g_slot_mutex);
-        for (int s = 0; s < LBMK_SLOTS; ++s)
-            if (!g_slot_used[s]) { slot = s; g_slot_used[s] = true; break; }
-    }
-    if (slot < 0) return LBM_ERR_UNSUPPORTED;
+    int err = LBM_OK;
+    const int slot = acquire_slot(lat->precision, mc, (cudaStream_t)cuda_stream, &err);
+    if (slot < 0) return err;
 
     lbm_ctx *c = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
     if (!c) {
-        std::lock_guard<std::mutex> lk(g_slot_mutex);
-        g_slot_used[slot] = false;
+        release_slot(lat->precision, slot);
         return LBM_ERR_ARG;
     }
     c->lat = *lat;
@@ -194,11 +276,26 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     c->ghost = bufs->ghost;
     c->pop_bytes = need_pop;
     c->mc = mc;
+    c->lat.seg_nx = nullptr;     // read here only
     int st = check_cuda(cudaMalloc((void **)&c->status, 16));
     if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
-    if (st == LBM_OK) {
-        const int e = ops(lat->precision).upload(slot, c->mc, c->stream);
-        st = e ? LBM_ERR_CUDA : LBM_OK;
+    if (st == LBM_OK && lat->nseg > 1) {
+        // per-x and per-lattice ranges of the batch
+        const int nx = lat->nx, ns = lat->nseg;
+        int4 *hx = (int4 *)malloc((size_t)nx * sizeof(int4));
+        int2 *hs = (int2 *)malloc((size_t)ns * sizeof(int2));
+        if (!hx || !hs) st = LBM_ERR_ARG;
+        for (int k = 0, x0 = 0; st == LBM_OK && k < ns; x0 += lat->seg_nx[k], ++k) {
+            hs[k] = make_int2(x0, x0 + lat->seg_nx[k]);
+            for (int x = x0; x < x0 + lat->seg_nx[k]; ++x) hx[x] = make_int4(x0, x0 + lat->seg_nx[k], k, 0);
+        }
+        if (st == LBM_OK) st = check_cuda(cudaMalloc((void **)&c->xseg, (size_t)nx * sizeof(int4)));
+        if (st == LBM_OK) st = check_cuda(cudaMalloc((void **)&c->segs, (size_t)ns * sizeof(int2)));
+        if (st == LBM_OK) st = check_cuda(cudaMemcpy(c->xseg, hx, (size_t)nx * sizeof(int4), cudaMemcpyHostToDevice));
+        if (st == LBM_OK) st = check_cuda(cudaMemcpy(c->segs, hs, (size_t)ns * sizeof(int2), cudaMemcpyHostToDevice));
+        if (st == LBM_OK) c->nseg = ns;
+        free(hx);
+        free(hs);
     }
     if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
     if (st != LBM_OK) {
@@ -216,7 +313,7 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
     const bool dX = is_device_ptr(X), dT = is_device_ptr(T), du = u ? is_device_ptr(u) : dX;
     if (dX != dT || dX != du) return LBM_ERR_ARG;     // all host or all device
     int st = LBM_OK;
-    if (is_mixed(c->lat.precision)) {
+    if (is_mixed(c->lat.precision) && !c->refs_fixed) {
         // rest states from the mean initial state
         const double *hX = X, *hT = T;
         double *tmpX = nullptr, *tmpT = nullptr;
@@ -231,7 +328,7 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
         }
         if (st == LBM_OK) {
             choose_references(c->mc, c->M, hX, hT, P, N);
-            st = ops(c->lat.precision).upload(c->slot, c->mc, c->stream) ? LBM_ERR_CUDA : LBM_OK;
+            st = reslot(c);
         }
         free(tmpX);
         free(tmpT);
@@ -273,6 +370,45 @@ int lbm_step_async(lbm_ctx *c, int n)
         c->cur = 1 - c->cur;
     }
     return LBM_OK;
+}
+
+int lbm_step_graph(lbm_ctx *c, int n)
+{
+    if (!c || n < 0) return LBM_ERR_ARG;
+    if (c->stream == nullptr) return LBM_ERR_UNSUPPORTED;   // the legacy default stream cannot be captured
+    if (!c->graph) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
+        const int cur0 = c->cur;
+        int e = 0;
+        for (int t = 0; t < 2 && !e; ++t) {
+            StepArgs a = args_of(c);
+            e = ops(c->lat.precision).step(a, nullptr);
+            c->cur = 1 - c->cur;
+        }
+        c->cur = cur0;
+        const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        if (e || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return LBM_ERR_CUDA;
+        }
+        cudaGraphExec_t x = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return LBM_ERR_CUDA;
+        c->graph = x;
+        c->graph_cur = cur0;
+    }
+    int left = n;
+    if (left > 0 && c->cur != c->graph_cur) {
+        const int st = lbm_step_async(c, 1);
+        if (st != LBM_OK) return st;
+        --left;
+    }
+    for (; left >= 2; left -= 2)          // two steps leave cur where it was
+        if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    return left == 1 ? lbm_step_async(c, 1) : LBM_OK;
 }
 
 int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
@@ -405,17 +541,37 @@ int lbm_get_populations(lbm_ctx *c, double *host_out)
 
 void *lbm_state_buffer(lbm_ctx *c) { return c ? c->buf[c->cur] : nullptr; }
 
+int lbm_get_references(const lbm_ctx *c, float *ref)
+{
+    if (!c || !ref) return LBM_ERR_ARG;
+    if (!is_mixed(c->lat.precision)) return LBM_ERR_UNSUPPORTED;
+    for (int s = 0; s < c->M; ++s)
+        for (int i = 0; i < LBMK_Q; ++i) ref[s * LBMK_Q + i] = c->mc.ref[s][i];
+    return LBM_OK;
+}
+
+int lbm_set_references(lbm_ctx *c, const float *ref)
+{
+    if (!c || !ref) return LBM_ERR_ARG;
+    if (!is_mixed(c->lat.precision)) return LBM_ERR_UNSUPPORTED;
+    for (int s = 0; s < c->M; ++s)
+        for (int i = 0; i < LBMK_Q; ++i) {
+            if (!isfinite(ref[s * LBMK_Q + i])) return LBM_ERR_ARG;
+            c->mc.ref[s][i] = i == 13 ? 0.0f : ref[s * LBMK_Q + i];   // rest populations are stored in double
+        }
+    c->refs_fixed = true;
+    return reslot(c);
+}
+
 int lbm_destroy(lbm_ctx *c)
 {
     if (!c) return LBM_ERR_ARG;
-    if (c->status) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(c->status);
-    }
-    {
-        std::lock_guard<std::mutex> lk(g_slot_mutex);
-        if (c->slot >= 0 && c->slot < LBMK_SLOTS) g_slot_used[c->slot] = false;
-    }
+    if (c->status || c->xseg || c->segs || c->graph) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->status) cudaFree(c->status);
+    if (c->xseg) cudaFree(c->xseg);
+    if (c->segs) cudaFree(c->segs);
+    release_slot(c->lat.precision, c->slot);
     free(c);
     return LBM_OK;
 }

@@ -63,14 +63,19 @@ __host__ __device__ constexpr size_t macro_bytes_for(int M, size_t N, size_t rea
 //   On the low-temperature lattice the rest population carries most of a
 //   set's mass (a factor 1 - R T per axis), and the energy populations fix
 //   the temperature that the Arrhenius rates amplify, so these stay double.
-// Ghost planes (x faces): [2][S][27][ny nz] doubles in both precisions.
+// Ghost planes (x faces): [2 G][S][27][ny nz] doubles in both precisions,
+// G lattices side by side in x (plane 2k: left face of lattice k, 2k+1:
+// right face).
 __host__ __device__ constexpr size_t pop_float_bytes(int M, size_t N) { return ((size_t)M * 27 * N * 4 + 15) & ~(size_t)15; }
 __host__ __device__ constexpr size_t pop_bytes_for(int S, size_t N, bool mixed)
 {
     return mixed ? pop_float_bytes(S - 1, N) + (size_t)(S - 1) * N * sizeof(double) + (size_t)27 * N * sizeof(double)
                  : (size_t)S * 27 * N * sizeof(double);
 }
-__host__ __device__ constexpr size_t ghost_bytes_for(int S, size_t plane) { return 2 * (size_t)S * 27 * plane * sizeof(double); }
+__host__ __device__ constexpr size_t ghost_bytes_for(int S, size_t plane, int nlat = 1)
+{
+    return 2 * (size_t)nlat * S * 27 * plane * sizeof(double);
+}
 
 // Everything the kernels read from constant memory for one context.
 //   H_a(T) = sum_k hco[a][k] T^(k+1) (k = 0..4) + hco[a][5]
@@ -102,6 +107,12 @@ struct MechConst {
 
 struct StepArgs {
     int slot, M, nx, ny, nz, N, bc_x;
+    // Lattices side by side in x (nseg >= 2): per x coordinate its lattice's
+    // x range and index {x0, x1, k, 0}; per lattice its range {x0, x1}.
+    // Null for one lattice (x0 = 0, x1 = nx, k = 0).
+    int nseg;
+    const int4 *xseg;
+    const int2 *segs;
     const void *src;     // populations read (pull)
     void *dst;           // populations written
     double *macro;       // double rows, then the storage-type record rows

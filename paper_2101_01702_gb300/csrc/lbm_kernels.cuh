@@ -92,8 +92,11 @@ __host__ __device__ constexpr double W1(int c) { return c == 0 ? 2.0 / 3.0 : 1.0
 __host__ __device__ constexpr double WI(int i) { return W1(CX(i)) * W1(CY(i)) * W1(CZ(i)); }
 constexpr int REST = 13;
 
+// A lattice node and the x range [x0, x1) of the lattice it belongs to
+// (lattice k of a batch placed side by side in x).
 struct Node {
     int n, x, y, z;
+    int x0, x1, k;
 };
 
 template <int I>
@@ -183,41 +186,47 @@ __device__ __forceinline__ double load_g(const PopView &v, int i, size_t idx)
 
 // Where a pulled population comes from: s(x) = s_post(x - c).
 struct PullIdx {
-    int xs[3];    // x - c for c = -1, 0, 1 (may be -1 or nx for ghosts)
+    int xs[3];    // x - c for c = -1, 0, 1
+    int gp[3];    // ghost plane of x - c (2k left, 2k+1 right face of lattice k), -1 inside
     int yz[9];    // y' + ny z' for (cy, cz)
 };
 
 __device__ __forceinline__ void make_pull(PullIdx &p, const Node &nd, const StepArgs &a)
 {
     for (int c = -1; c <= 1; ++c) {
-        int xs = nd.x - c;
+        int xs = nd.x - c, gp = -1;
         if (a.bc_x == 0) xs = wrapi(xs, a.nx);
+        else if (xs < nd.x0) gp = 2 * nd.k;
+        else if (xs >= nd.x1) gp = 2 * nd.k + 1;
         p.xs[c + 1] = xs;
+        p.gp[c + 1] = gp;
     }
     for (int cz = -1; cz <= 1; ++cz)
         for (int cy = -1; cy <= 1; ++cy)
             p.yz[(cy + 1) + 3 * (cz + 1)] = wrapi(nd.y - cy, a.ny) + a.ny * wrapi(nd.z - cz, a.nz);
 }
 
-// Source of direction i: a buffer node, or (side, plane index) of a ghost.
+// Source of direction i: a buffer node, or (ghost plane, index in the plane).
 struct Src {
     bool ghost;
-    int side;
+    int side;     // ghost plane (see PullIdx::gp)
     size_t idx;
 };
 
 __device__ __forceinline__ Src src_of(int i, const PullIdx &p, const StepArgs &a)
 {
     const int xs = p.xs[CX(i) + 1];
+    const int gp = p.gp[CX(i) + 1];
     const int yz = p.yz[(CY(i) + 1) + 3 * (CZ(i) + 1)];
-    if (a.bc_x == 1 && (xs < 0 || xs >= a.nx)) return Src{true, xs < 0 ? 0 : 1, (size_t)yz};
+    if (gp >= 0) return Src{true, gp, (size_t)yz};
     return Src{false, 0, (size_t)xs + (size_t)a.nx * yz};
 }
 
-__device__ __forceinline__ double load_ghost(const StepArgs &a, int side, int s, int i, size_t yz)
+__device__ __forceinline__ double load_ghost(const StepArgs &a, int plane_idx, int s, int i, size_t yz)
 {
     const size_t plane = (size_t)a.ny * a.nz;
-    return __ldg(static_cast<const double *>(a.ghost) + ((size_t)(side * (a.M + 1) + s) * LBMK_Q + i) * plane + yz);
+    return __ldg(static_cast<const double *>(a.ghost) + ((size_t)(plane_idx * (a.M + 1) + s) * LBMK_Q + i) * plane +
+                 yz);
 }
 
 __device__ __forceinline__ Real pull_sf(const MechConst &mc, const PopView &v, const StepArgs &a, int s, int i,
@@ -271,7 +280,8 @@ __device__ __forceinline__ void store_g(void *buf, const StepArgs &a, int i, siz
 #endif
 }
 
-// Stencil neighbours x + c (periodic, or clamped for zero-gradient x faces).
+// Stencil neighbours x + c (periodic, or clamped to the node's own lattice
+// for zero-gradient x faces).
 struct StencilIdx {
     int xs[3];
     int row[9];
@@ -282,7 +292,7 @@ __device__ __forceinline__ void make_stencil(StencilIdx &t, const Node &nd, cons
     for (int c = -1; c <= 1; ++c) {
         int xn = nd.x + c;
         if (a.bc_x == 0) xn = wrapi(xn, a.nx);
-        else xn = xn < 0 ? 0 : (xn >= a.nx ? a.nx - 1 : xn);
+        else xn = xn < nd.x0 ? nd.x0 : (xn >= nd.x1 ? nd.x1 - 1 : xn);
         t.xs[c + 1] = xn;
     }
     for (int cz = -1; cz <= 1; ++cz)
@@ -431,6 +441,16 @@ __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
     const int r = nd.n / a.nx;
     nd.y = r % a.ny;
     nd.z = r / a.ny;
+    if (a.xseg) {
+        const int4 e = __ldg(a.xseg + nd.x);
+        nd.x0 = e.x;
+        nd.x1 = e.y;
+        nd.k = e.z;
+    } else {
+        nd.x0 = 0;
+        nd.x1 = a.nx;
+        nd.k = 0;
+    }
     return true;
 }
 
@@ -537,10 +557,18 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
 {
     const MechConst &mc = c_mech[a.slot];
     const int plane = a.ny * a.nz;
+    const int nlat = a.nseg > 1 ? a.nseg : 1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 2 * plane) return;
-    const int side = t / plane, yz = t % plane;
-    const size_t n = (size_t)(side ? a.nx - 1 : 0) + (size_t)a.nx * yz;
+    if (t >= 2 * nlat * plane) return;
+    const int gp = t / plane, yz = t % plane;          // ghost plane 2k + side of lattice k
+    const int side = gp & 1, k = gp >> 1;
+    int x0 = 0, x1 = a.nx;
+    if (a.segs) {
+        const int2 r = __ldg(a.segs + k);
+        x0 = r.x;
+        x1 = r.y;
+    }
+    const size_t n = (size_t)(side ? x1 - 1 : x0) + (size_t)a.nx * yz;
     const PopView v = view(a.src, a);
     double rho_a[M], rho = 0.0, j[3] = {0, 0, 0}, rhoE = 0.0;
     double rest = 0.0;
@@ -568,7 +596,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
     mixture_energy_poly<M>(mc, Y, eu);
     const double T = solve_T(eu, e, a.macro[(size_t)DR_T * a.N + n], a.status);
     if (side == 0) u[0] = u[1] = u[2] = 0.0;
-    double *gh = static_cast<double *>(a.ghost) + (size_t)side * (M + 1) * LBMK_Q * plane;
+    double *gh = static_cast<double *>(a.ghost) + (size_t)gp * (M + 1) * LBMK_Q * plane;
     equilibria<M>(mc, rho_a, u, T, [&](int s, int i, double val) { gh[((size_t)s * LBMK_Q + i) * plane + yz] = val; });
 }
 
@@ -942,12 +970,14 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     a.macro[(size_t)dr_gtr(M) * N + n] = tr3;
 #if LBMK_MIXED
     // rest-direction equilibria of the species and mixture sets (Eqs. (feq), (feqmix))
+    {
+        const double c2[3] = {1.0 - u[0] * u[0], 1.0 - u[1] * u[1], 1.0 - u[2] * u[2]};
 #pragma unroll
-    for (int s = 0; s < M; ++s) {
-        const double z = (s < M - 1 ? mc.Ra[s] : Rm) * T;
-        const double r = s < M - 1 ? rho_a[s] : rho;
-        a.macro[(size_t)(DR_FEQ0 + s) * N + n] =
-            r * (1.0 - (u[0] * u[0] + z)) * (1.0 - (u[1] * u[1] + z)) * (1.0 - (u[2] * u[2] + z));
+        for (int s = 0; s < M; ++s) {
+            const double z = (s < M - 1 ? mc.Ra[s] : Rm) * T;
+            const double r = s < M - 1 ? rho_a[s] : rho;
+            a.macro[(size_t)(DR_FEQ0 + s) * N + n] = r * (c2[0] - z) * (c2[1] - z) * (c2[2] - z);
+        }
     }
 #endif
     // storage-type rows
@@ -965,9 +995,10 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
         R[(size_t)(rr.y + s) * N + n] = (Real)Yr[s];
 #pragma unroll
         for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = (Real)du[s][d];
-        // beta_a = 1/(2 tau_a + 1), Eq. (fStar)
-        const SReal it = ita[s];
-        R[(size_t)(rr.beta + s) * N + n] = (Real)(it / ((SReal)2 + it));
+        // beta_a = 1/(2 tau_a + 1), Eq. (fStar): a parameter of the species
+        // collision, formed in the storage type it is used in
+        const Real it = (Real)ita[s];
+        R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
         R[(size_t)(rr.h + s) * N + n] = (Real)Ha[s];
     }
     R[(size_t)rr.rho * N + n] = (Real)rho;
@@ -1331,7 +1362,7 @@ int run_step(const StepArgs &a, cudaEvent_t *ev)
     if (ev) cudaEventRecord(ev[0], a.stream);
     if (a.bc_x == 1) {
         const int plane = a.ny * a.nz;
-        k_ghost<M><<<grid_for(2 * plane), LBMK_BLOCK, 0, a.stream>>>(a);
+        k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
     }
     if (ev) cudaEventRecord(ev[1], a.stream);
     k_pre<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
@@ -1351,7 +1382,7 @@ int run_moments(const StepArgs &a, unsigned mask, double *out)
 {
     if (a.bc_x == 1) {
         const int plane = a.ny * a.nz;
-        k_ghost<M><<<grid_for(2 * plane), LBMK_BLOCK, 0, a.stream>>>(a);
+        k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
     }
     k_moments<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, mask, out);
     return (int)cudaGetLastError();

@@ -43,7 +43,8 @@ _ip = C.POINTER(C.c_int)
 
 
 class lbm_lattice(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc_x", C.c_int), ("precision", C.c_int)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("bc_x", C.c_int), ("precision", C.c_int),
+                ("nseg", C.c_int), ("seg_nx", C.POINTER(C.c_int))]
 
 
 class lbm_species(C.Structure):
@@ -71,6 +72,9 @@ _lib.lbm_create.argtypes = [C.POINTER(lbm_lattice), C.POINTER(lbm_species), C.PO
 _lib.lbm_init.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]
 _lib.lbm_step.argtypes = [C.c_void_p, C.c_int]
 _lib.lbm_step_async.argtypes = [C.c_void_p, C.c_int]
+_lib.lbm_step_graph.argtypes = [C.c_void_p, C.c_int]
+_lib.lbm_get_references.argtypes = [C.c_void_p, C.c_void_p]
+_lib.lbm_set_references.argtypes = [C.c_void_p, C.c_void_p]
 _lib.lbm_sync.argtypes = [C.c_void_p]
 _lib.lbm_step_timed.argtypes = [C.c_void_p, C.c_int, _dp]
 _lib.lbm_moments.argtypes = [C.c_void_p, C.c_uint, C.c_void_p]
@@ -85,9 +89,11 @@ _lib.lbm_step_fixed_scratch.argtypes = [C.POINTER(lbm_lattice), C.POINTER(lbm_sp
 _lib.lbm_strerror.argtypes = [C.c_int]
 _lib.lbm_strerror.restype = C.c_char_p
 
-EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_timed", "lbm_sync",
+EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_graph",
+            "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
-            "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check"]
+            "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
+            "lbm_set_references"]
 
 
 def library_path() -> str:
@@ -133,6 +139,20 @@ def lbm_step(ctx, n: int) -> int:
 
 def lbm_step_async(ctx, n: int) -> int:
     return _lib.lbm_step_async(ctx, int(n))
+
+
+def lbm_step_graph(ctx, n: int) -> int:
+    return _lib.lbm_step_graph(ctx, int(n))
+
+
+def lbm_get_references(ctx, ref: np.ndarray) -> int:
+    assert ref.dtype == np.float32 and ref.flags.c_contiguous
+    return _lib.lbm_get_references(ctx, ref.ctypes.data)
+
+
+def lbm_set_references(ctx, ref: np.ndarray) -> int:
+    ref = np.ascontiguousarray(ref, dtype=np.float32)
+    return _lib.lbm_set_references(ctx, ref.ctypes.data)
 
 
 def lbm_step_timed(ctx, n: int, phase_ms: np.ndarray) -> int:
@@ -218,7 +238,11 @@ class Solver:
             self._keep.append(a)
             return a.ctypes.data_as(_ip)
 
-        self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision)
+        seg = getattr(lattice, "seg_nx", None)
+        if seg is not None and len(seg) > 1:
+            self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision, len(seg), i(seg))
+        else:
+            self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision, 0, None)
         self.sp = lbm_species(self.M, d(species.W), species.thermo, d(species.cp_R), d(species.h_form),
                               species.T0, d(species.poly7), d(species.D), species.nu, species.Pr,
                               species.r_lat, species.visc_model)
@@ -281,6 +305,19 @@ class Solver:
 
     def step_async(self, n: int = 1):
         _check(lbm_step_async(self.ctx, n), "lbm_step_async")
+
+    def references(self) -> np.ndarray:
+        """Rest references of the mixed modes, float32 [M, 27]."""
+        ref = np.zeros((self.M, 27), dtype=np.float32)
+        _check(lbm_get_references(self.ctx, ref), "lbm_get_references")
+        return ref
+
+    def set_references(self, ref):
+        _check(lbm_set_references(self.ctx, ref), "lbm_set_references")
+
+    def step_graph(self, n: int = 1):
+        """n steps through the captured two-step CUDA graph (no wait)."""
+        _check(lbm_step_graph(self.ctx, n), "lbm_step_graph")
 
     def step_timed(self, n: int = 1):
         """Runs n steps; returns per-phase device milliseconds summed over

@@ -68,3 +68,29 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert raw.lbm_create(None, None, None, None, None, None) == lib.LBM_ERR_ARG
     assert lib.lbm_strerror(lib.LBM_ERR_NEGATIVE) == "negative species density"
     assert lib.lbm_strerror(12345) == "unknown status"
+
+
+def test_buffer_sizes_of_a_batch_of_lattices(lib):
+    import workload as w
+    p = w.sphere3d_problem(n=8, radius=2)
+    W = np.ascontiguousarray(p.species.W)
+    sp = lib.lbm_species(9, W.ctypes.data_as(C.POINTER(C.c_double)), 1, None, None, 298.15, None, None,
+                         0.8, 0.71, p.species.r_lat, 1)
+    seg = (C.c_int * 3)(37, 64, 129)
+    lat = lib.lbm_lattice(230, 4, 4, 1, lib.LBM_FP64, 3, C.cast(seg, C.POINTER(C.c_int)))
+    pop, mac, gh = lib.lbm_buffer_sizes(lat, sp)
+    N = 230 * 16
+    assert pop == 10 * 27 * N * 8
+    assert gh == 2 * 3 * 10 * 27 * 16 * 8           # two ghost faces per lattice
+    bad = []
+    seg_short = (C.c_int * 3)(37, 64, 128)          # lengths must add up to nx
+    bad.append(lib.lbm_lattice(230, 4, 4, 1, lib.LBM_FP64, 3, C.cast(seg_short, C.POINTER(C.c_int))))
+    bad.append(lib.lbm_lattice(230, 4, 4, 0, lib.LBM_FP64, 3, C.cast(seg, C.POINTER(C.c_int))))  # periodic x
+    seg_zero = (C.c_int * 3)(0, 101, 129)
+    bad.append(lib.lbm_lattice(230, 4, 4, 1, lib.LBM_FP64, 3, C.cast(seg_zero, C.POINTER(C.c_int))))
+    bad.append(lib.lbm_lattice(230, 4, 4, 1, lib.LBM_FP64, 3, None))
+    for b in bad:
+        with pytest.raises(lib.LBMError) as e:
+            lib.lbm_buffer_sizes(b, sp)
+        assert e.value.status == lib.LBM_ERR_ARG
+

@@ -14,6 +14,8 @@ from .configs import (  # noqa: F401
     sphere3d_problem,
     small_periodic_problem,
     batched_flames_lengths,
+    batched_flames_problem,
+    flame_of_batch,
     mech9,
     mech3,
 )

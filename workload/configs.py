@@ -341,3 +341,52 @@ def batched_flames_lengths(count: int = 48, seed: int = 48):
     L = rng.integers(256, 4097, size=count)
     phi = rng.uniform(0.5, 3.0, size=count)
     return L, phi
+
+
+def batched_flames_problem(count: int = 48, seed: int = 48, ny: int = 4, nz: int = 4, lengths=None, phis=None,
+                           T_u: float = MECH9_T_UNBURNT, T_slab: float = 1500.0, slab_frac: float = 0.2,
+                           chem_scale: float = MECH9_CHEM_SCALE) -> Problem:
+    """Independent quasi-1D flames side by side along x in one lattice.
+
+    Flame k has L_k x ny x nz nodes (lengths and equivalence ratios from
+    batched_flames_lengths(count, seed) unless given), each set up as
+    flame1d_problem: its unburnt mixture at T_u, the rightmost slab_frac of
+    its own x range at T_slab, uniform pressure, at rest, with ghost-node
+    faces of its own on both x ends.  lattice.seg_nx holds the lengths.
+    """
+    if lengths is None or phis is None:
+        L, ph = batched_flames_lengths(count, seed)
+        lengths = L if lengths is None else lengths
+        phis = ph if phis is None else phis
+    lengths = [int(v) for v in lengths]
+    phis = [float(v) for v in phis]
+    sp, mech = mech9(chem_scale)
+    nx = sum(lengths)
+    N = nx * ny * nz
+    xs = np.arange(N) % nx
+    X = np.empty((9, N))
+    T = np.full(N, T_u)
+    x0 = 0
+    for Lk, phk in zip(lengths, phis):
+        sel = (xs >= x0) & (xs < x0 + Lk)
+        X[:, sel] = _normalise_with_noise(phi_mixture(phk), 1, None)[:, :1]
+        T[sel & (xs >= x0 + int(round((1.0 - slab_frac) * Lk)))] = T_slab
+        x0 += Lk
+    return Problem(f"flames{len(lengths)}_{nx}x{ny}x{nz}_M9",
+                   LatticeSpec(nx, ny, nz, BC_EQ_ZEROGRAD_U0LEFT, seg_nx=lengths),
+                   sp, mech, InitFields(X=np.ascontiguousarray(X), T=T, u=None, P=mech.P0), steps=5000)
+
+
+def flame_of_batch(prob: Problem, k: int) -> Problem:
+    """Flame k of a batched_flames_problem as a lattice of its own."""
+    lat = prob.lattice
+    x0 = sum(lat.seg_nx[:k])
+    Lk = lat.seg_nx[k]
+    N = lat.nx * lat.ny * lat.nz
+    xs = np.arange(N) % lat.nx
+    sel = (xs >= x0) & (xs < x0 + Lk)
+    X = np.ascontiguousarray(prob.init.X[:, sel])
+    T = np.ascontiguousarray(prob.init.T[sel])
+    return Problem(f"{prob.name}_flame{k}", LatticeSpec(Lk, lat.ny, lat.nz, lat.bc_x), prob.species, prob.mech,
+                   InitFields(X=X, T=T, u=None, P=prob.init.P), steps=prob.steps)
+

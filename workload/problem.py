@@ -31,6 +31,9 @@ class LatticeSpec:
     ny: int
     nz: int
     bc_x: int = BC_PERIODIC  # y and z are always periodic
+    # independent lattices side by side in x (lengths summing to nx), each
+    # with its own boundary faces; None for a single lattice
+    seg_nx: Optional[list] = None
 
     @property
     def n_nodes(self) -> int:
