@@ -190,7 +190,7 @@ def run_ours(args):
     import workload as w
     from paper_2101_01702_gb300 import build
     build.build()
-    from paper_2101_01702_gb300 import lbm
+    from paper_2101_01702_gb300 import lbm, replicas
 
     n = args.size
     prob = w.sphere3d_problem(n=n, radius=20.0 * n / 256.0)
@@ -229,11 +229,8 @@ def run_ours(args):
     barrier()
     ms = float(ph[lbm.LBM_PHASES])
     phases = ph[:lbm.LBM_PHASES] / args.steps            # ms per launch: ghost, pre, chem, grad, step
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    ms = replicas.max_over_ranks(ms, dist, "cuda")        # the job is as slow as its slowest replica
+    mlups = replicas.whole_job_mlups([N] * world, args.steps, ms)
 
     # ---- rooflines --------------------------------------------------------
     # The step is bound by FP64 arithmetic (temperature iteration, energy
@@ -364,33 +361,51 @@ def run_ours(args):
 def run_flames(args):
     """The batched quasi-1D flames: 48 ragged flames side by side in one
     lattice, stepped with one set of launches per step (plain and through a
-    captured CUDA graph), against the same 48 flames stepped one flame at a
-    time (one context per flame, sharing the batch's tables)."""
+    captured CUDA graph), against the same flames stepped one flame at a
+    time (one context per flame, sharing the batch's tables).  With N ranks
+    the flames are split across them by node count (no collective on the
+    data path); the value counts all ranks' nodes over the slowest rank."""
     import torch
     import workload as w
     from paper_2101_01702_gb300 import build
     build.build()
-    from paper_2101_01702_gb300 import lbm
+    from paper_2101_01702_gb300 import lbm, replicas
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     modes = {"mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST, "fp64": lbm.LBM_FP64}
     precision = modes[args.precision]
-    prob = w.batched_flames_problem()
+    L_all, phi_all = w.batched_flames_lengths()
+    shards = replicas.shard_lengths(L_all, world)
+    mine = shards[rank]
+    prob = w.batched_flames_problem(lengths=[L_all[k] for k in mine], phis=[phi_all[k] for k in mine])
     N = prob.lattice.n_nodes
     K = args.steps
     stream = torch.cuda.Stream()
 
     def timed(fn):
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
+        if dist is not None:
+            dist.barrier()
+        return replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
 
     batch = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
     batch.step(args.warmup)
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         ms_plain = timed(lambda: batch.step_async(K))
         batch.step_graph(2)                       # capture outside the timed region
         assert batch.sync() == lbm.LBM_OK
@@ -420,20 +435,25 @@ def run_flames(args):
         assert s.sync() == lbm.LBM_OK
         s.close()
 
-    mlups = lambda ms: N * K / (ms * 1e-3) / 1e6
-    line = {"metric": "MLUPS (batched quasi-1D flames, one launch set per step)", "value": mlups(ms_graph),
-            "unit": "MLUPS", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms_graph / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if precision != lbm.LBM_FP64 else "f64", "data": "synthetic",
-            "config": {"workload": f"flames{len(prob.lattice.seg_nx)}_M9_{args.precision}", "nodes": N,
-                       "flames": len(prob.lattice.seg_nx), "lengths": [min(prob.lattice.seg_nx),
-                                                                         max(prob.lattice.seg_nx)],
-                       "cross_section": "4x4"},
-            "batched_graph_mlups": mlups(ms_graph), "batched_plain_mlups": mlups(ms_plain),
-            "loop_single_flames_mlups": mlups(ms_loop), "speedup_vs_loop": ms_loop / ms_graph,
-            "gpu_launches": K * 6,      # ghost, moments, rates, gradients, energy and species collisions
-            "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    nodes = [sum(int(L_all[k]) for k in shards[r]) * prob.lattice.ny * prob.lattice.nz for r in range(world)]
+    mlups = lambda ms: replicas.whole_job_mlups(nodes, K, ms)
+    if rank == 0:
+        line = {"metric": "MLUPS (batched quasi-1D flames, one launch set per step)", "value": mlups(ms_graph),
+                "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
+                "ms_per_step": ms_graph / K, "higher_is_better": True,
+                "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if precision != lbm.LBM_FP64 else "f64", "data": "synthetic",
+                "config": {"workload": f"flames{len(L_all)}_M9_{args.precision}", "nodes": sum(nodes),
+                           "flames": len(L_all), "lengths": [int(min(L_all)), int(max(L_all))],
+                           "cross_section": "4x4", "parallelism": f"flames split over {world} ranks"
+                           if world > 1 else "single_gpu"},
+                "batched_graph_mlups": mlups(ms_graph), "batched_plain_mlups": mlups(ms_plain),
+                "loop_single_flames_mlups": mlups(ms_loop), "speedup_vs_loop": ms_loop / ms_graph,
+                "gpu_launches": K * 6,      # ghost, moments, rates, gradients, energy and species collisions
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
