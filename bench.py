@@ -40,14 +40,14 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions;
 #   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 FP64_FLOPS_PER_NODE = {
-    "mixed": {"k_pre": None, "k_chem": None, "k_step": None},
-    "mixed_fast": {"k_pre": 747.0, "k_chem": 679.0, "k_step": 217.0},
-    "fp64": {"k_pre": 2859.4, "k_chem": 1630.0, "k_step": 17441.0},
+    "mixed": {"k_pre": 2079.2, "k_chem": 1236.0, "k_step_g": 163.0, "k_step": 18.0},
+    "mixed_fast": {"k_pre": 723.0, "k_chem": 646.0, "k_step_g": 163.0, "k_step": 18.0},
+    "fp64": {"k_pre": 2859.4, "k_chem": 1236.0, "k_step_g": 737.0, "k_step": 12534.0},
 }
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": None, "k_chem": None, "k_step": None},
-    "mixed_fast": {"k_pre": 2200.3, "k_chem": 64.4, "k_step": 2955.4},
-    "fp64": {"k_pre": 3410.3, "k_chem": 138.2, "k_step": 5148.7},
+    "mixed": {"k_pre": 2961.1, "k_chem": 64.8, "k_step_g": 600.2, "k_step": 2402.6},
+    "mixed_fast": {"k_pre": 2202.6, "k_chem": 64.5, "k_step_g": 600.2, "k_step": 2402.2},
+    "fp64": {"k_pre": 3409.6, "k_chem": 138.2, "k_step_g": 699.8, "k_step": 4464.2},
 }
 
 
@@ -228,7 +228,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ms = float(ph[lbm.LBM_PHASES])
-    phases = ph[:lbm.LBM_PHASES] / args.steps            # ms per launch: ghost, pre, chem, grad, step
+    phases = ph[:lbm.LBM_PHASES] / args.steps            # ms per launch: ghost, pre, chem, grad, step_g, step
     ms = replicas.max_over_ranks(ms, dist, "cuda")        # the job is as slow as its slowest replica
     mlups = replicas.whole_job_mlups([N] * world, args.steps, ms)
 
@@ -241,7 +241,8 @@ def run_ours(args):
     mixed = precision != lbm.LBM_FP64
     alg_bytes_node = 2 * stored_bytes_per_node(M, mixed)
     step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
-    kern_ms = {"k_pre": phases[1], "k_chem": phases[2], "k_grad": phases[3], "k_step": phases[4]}
+    kern_ms = {"k_pre": phases[1], "k_chem": phases[2], "k_grad": phases[3], "k_step_g": phases[4],
+               "k_step": phases[5]}
     flops = FP64_FLOPS_PER_NODE[args.precision]
     dram = DRAM_BYTES_PER_NODE[args.precision]
     kernels = {}
@@ -253,7 +254,7 @@ def run_ours(args):
         if dram.get(k):
             e["dram_gbs"] = dram[k] * N / (t * 1e-3) / 1e9
         kernels[k] = e
-    dom = max(("k_pre", "k_chem", "k_step"), key=lambda k: kern_ms[k])
+    dom = max(("k_pre", "k_chem", "k_step_g", "k_step"), key=lambda k: kern_ms[k])
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom].get("fp64_tflops"),
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kernels[dom].get("fp64_frac"),
                 "traffic": dram[dom] * N if dram.get(dom) else None,
@@ -304,7 +305,8 @@ def run_ours(args):
         msf = float(phf[lbm.LBM_PHASES])
         phf = phf[:lbm.LBM_PHASES] / args.steps
         fast = {"mlups": N * args.steps * world / (msf * 1e-3) / 1e6, "steps": args.steps,
-                "phase_ms": {"moments": phf[1], "chemistry": phf[2], "gradients": phf[3], "collision": phf[4]},
+                "phase_ms": {"moments": phf[1], "chemistry": phf[2], "gradients": phf[3],
+                             "energy_collision": phf[4], "species_collision": phf[5]},
                 "note": "LBM_MIXED_FAST: Stefan-Maxwell solve and relaxation in float, exponentials of the "
                         "rates with a float 2^f; same storage and accuracy bar"}
         sf.close()
@@ -341,7 +343,7 @@ def run_ours(args):
                              % (stored_bytes_per_node(M, mixed) * N / 1e9)},
             "hbm_frac_step": step_frac,
             "phase_ms": {"ghost": phases[0], "moments": phases[1], "chemistry": phases[2],
-                         "gradients": phases[3], "collision": phases[4]},
+                         "gradients": phases[3], "energy_collision": phases[4], "species_collision": phases[5]},
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "kernels": kernels,
@@ -350,7 +352,7 @@ def run_ours(args):
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (5 + (prob.lattice.bc_x != 0)),
+            "gpu_launches": args.steps * (5 + (prob.lattice.bc_x != 0)),   # pre, chem, grad, step_g, step (+ghost)
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

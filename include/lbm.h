@@ -198,12 +198,12 @@ int lbm_step_graph(lbm_ctx *ctx, int n);
 
 /* lbm_step_async with CUDA events recorded on the stream between the
  * kernels of each step (all steps enqueued back to back, one wait at the
- * end).  phase_ms must hold LBM_PHASES + 1 doubles: phase_ms[0..4] receive
+ * end).  phase_ms must hold LBM_PHASES + 1 doubles: phase_ms[0..5] receive
  * the summed device time of the ghost-node, moment, production-rate,
- * gradient and collision kernels over the n steps, phase_ms[LBM_PHASES]
- * the device time from the first launch to the end of the last.  Returns
- * like lbm_step. */
-#define LBM_PHASES 5
+ * gradient, energy-collision and species/mixture-collision kernels over
+ * the n steps, phase_ms[LBM_PHASES] the device time from the first launch
+ * to the end of the last.  Returns like lbm_step. */
+#define LBM_PHASES 6
 int lbm_step_timed(lbm_ctx *ctx, int n, double *phase_ms);
 
 /* Waits for the stream and returns (then clears) the recorded error. */

@@ -133,8 +133,8 @@ int init_mixed(const StepArgs &a, const double *X, const double *T, const double
 int init_mixed_fast(const StepArgs &a, const double *X, const double *T, const double *u, double P);
 
 // one full time step src -> dst (ghost, moments, production rates,
-// gradients, collision); with ev != nullptr, events ev[0..5] are recorded
-// around the five phases
+// gradients, energy collision, species/mixture collision); with ev !=
+// nullptr, events ev[0..6] are recorded around the six phases
 int step_fp64(const StepArgs &a, cudaEvent_t *ev = nullptr);
 int step_mixed(const StepArgs &a, cudaEvent_t *ev = nullptr);
 int step_mixed_fast(const StepArgs &a, cudaEvent_t *ev = nullptr);

@@ -1135,7 +1135,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step_g(StepArgs a)
     const PopView v = view(a.src, a);
     PullIdx p;
     make_pull(p, nd, a);
-    double gcheck = 0.0;
+    int bad = 0;     // a non-finite result: all exponent bits set (integer test, no FP64 work)
     // row by row: j = (cy+1) + 3 (cz+1), then cx = -1, 0, 1 (i = (cx+1) + 3 j)
     for_dirs<0, 9>([&](auto dj) {
         constexpr int j = decltype(dj)::value, cy = j % 3 - 1, cz = j / 3 - 1;
@@ -1153,10 +1153,10 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step_g(StepArgs a)
             constexpr int k = decltype(dx)::value, I = k + 3 * j;
             const double val = fma(om1m, pull_g(v, a, I, p), B[k]);
             store_g(a.dst, a, I, n, val);
-            gcheck += val;
+            bad |= (__double2hiint(val) & 0x7ff00000) == 0x7ff00000;
         });
     });
-    if (!isfinite(gcheck)) flag(a.status, LBMK_BIT_NONFINITE);
+    if (bad) flag(a.status, LBMK_BIT_NONFINITE);
 }
 
 // ---------------------------------------------------------------------
@@ -1168,6 +1168,11 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_step_g(StepArgs a)
 template <int M>
 __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 {
+#if !LBMK_MIXED
+    // y-z factors of the species equilibria for the current row, this
+    // thread's column (kept in registers in the mixed units)
+    __shared__ double sh_yz[2 * M * LBMK_BLOCK];
+#endif
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
@@ -1243,7 +1248,10 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
     };
     if (kPrefetch) load_raw(0);
 
-    Real pe_yz[M], ps_yz[M], fe_yz = 0, AXyz = 0;
+#if LBMK_MIXED
+    Real pe_yz[M], ps_yz[M];
+#endif
+    Real fe_yz = 0, AXyz = 0;
     int cy = 0, cz = 0;
     auto yz_factors = [&](int s, Real z, Real &pe, Real &ps) {
         pe = psi_c(cy, u[1], u2[1] + z) * psi_c(cz, u[2], u2[2] + z);
@@ -1256,11 +1264,18 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
             cy = j % 3 - 1;
             cz = j / 3 - 1;
             const int nnz = (cy != 0) + (cz != 0);
-            // y-z factors of the species equilibria: kept across the row in
-            // float; recomputed per direction in double (register budget)
-            if (LBMK_MIXED) {
+            // y-z factors of the species equilibria, shared by the row's three
+            // directions: in registers (float) or shared memory (double)
 #pragma unroll
-                for (int s = 0; s < M; ++s) yz_factors(s, RA(s) * T, pe_yz[s], ps_yz[s]);
+            for (int s = 0; s < M; ++s) {
+#if LBMK_MIXED
+                yz_factors(s, RA(s) * T, pe_yz[s], ps_yz[s]);
+#else
+                Real pe, ps;
+                yz_factors(s, RA(s) * T, pe, ps);
+                sh_yz[(2 * s) * LBMK_BLOCK + threadIdx.x] = pe;
+                sh_yz[(2 * s + 1) * LBMK_BLOCK + threadIdx.x] = ps;
+#endif
             }
             fe_yz = rho * psi_c(cy, u[1], u2[1] + RT) * psi_c(cz, u[2], u2[2] + RT);
             // isotropy correction A_i . X (Eq. (Ai)): only |c_i| = 1
@@ -1281,9 +1296,12 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 #pragma unroll
         for (int s = 0; s < M; ++s) {
             const Real z = RA(s) * T;
-            Real pyz, syz;
-            if (LBMK_MIXED) { pyz = pe_yz[s]; syz = ps_yz[s]; }
-            else yz_factors(s, z, pyz, syz);
+#if LBMK_MIXED
+            const Real pyz = pe_yz[s], syz = ps_yz[s];
+#else
+            const Real pyz = sh_yz[(2 * s) * LBMK_BLOCK + threadIdx.x];
+            const Real syz = sh_yz[(2 * s + 1) * LBMK_BLOCK + threadIdx.x];
+#endif
             const Real pe = psi_c(cx, u[0], u2[0] + z) * pyz;
             const Real pst = psi_c(cx, xs[s][0], xs[s][0] * xs[s][0] + z) * syz;
             eqp[s] = pe;
@@ -1372,8 +1390,9 @@ int run_step(const StepArgs &a, cudaEvent_t *ev)
     k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[4], a.stream);
     k_step_g<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
     if (ev) cudaEventRecord(ev[5], a.stream);
+    k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
+    if (ev) cudaEventRecord(ev[6], a.stream);
     return (int)cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ LBM_MIXED = 1
 LBM_MIXED_FAST = 2
 LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2, 4, 8, 16, 32, 64
 LBM_F_RHO_DOT = 128
-LBM_PHASES = 5
+LBM_PHASES = 6
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -321,8 +321,9 @@ class Solver:
 
     def step_timed(self, n: int = 1):
         """Runs n steps; returns per-phase device milliseconds summed over
-        them (ghost, moments, production rates, gradients, collision) and,
-        last, the device milliseconds of the whole run."""
+        them (ghost, moments, production rates, gradients, energy collision,
+        species/mixture collision) and, last, the device milliseconds of the
+        whole run."""
         ph = np.zeros(LBM_PHASES + 1)
         _check(lbm_step_timed(self.ctx, n, ph), "lbm_step_timed")
         return ph
