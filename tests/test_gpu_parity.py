@@ -176,3 +176,41 @@ def test_production_rates_against_oracle(orc, lbm, precision, tol):
             continue
         err = np.abs(got[a] - ref[a]).max() / scale
         assert err <= tol, (a, err)
+
+
+def _binary_problem(bc_x):
+    """Two inert gases of unequal molar mass (W = 4, 28), no reactions, on a
+    ragged 37x5x3 box; random composition, temperature and velocity."""
+    from workload.problem import (InitFields, LatticeSpec, MechanismSpec, Problem, SpeciesSpec,
+                                  THERMO_CONST_CP, VISC_KINEMATIC)
+    W = np.array([4.0, 28.0])
+    D = np.array([[0.03, 0.03], [0.03, 0.03]])
+    sp = SpeciesSpec(names=["A", "B"], W=W, thermo=THERMO_CONST_CP, cp_R=np.array([2.5, 3.5]),
+                     h_form=np.zeros(2), T0=1.0, poly7=np.zeros((2, 7)), D=D, nu=0.02, Pr=0.71, r_lat=0.4,
+                     elements=np.eye(2, dtype=np.int32), element_names=["A", "B"], visc_model=VISC_KINEMATIC)
+    mech = MechanismSpec(nu_f=np.zeros((0, 2), np.int32), nu_r=np.zeros((0, 2), np.int32),
+                         log_A=np.zeros(0), b=np.zeros(0), theta=np.zeros(0), rtype=np.zeros(0, np.int32),
+                         eff=np.zeros((0, 2)), low=np.zeros((0, 3)), reversible=np.zeros(0, np.int32),
+                         T_ref=1.0, P0=1.0)
+    nx, ny, nz = 37, 5, 3
+    N = nx * ny * nz
+    rng = np.random.default_rng(22)
+    X1 = 0.3 + rng.uniform(-0.1, 0.1, N)
+    X = np.stack([X1, 1.0 - X1])
+    T = 1.0 + rng.uniform(-0.2, 0.2, N)
+    u = rng.uniform(-0.01, 0.01, (3, N))
+    lat = LatticeSpec(nx, ny, nz, bc_x)
+    return Problem("binary_37x5x3", lat, sp, mech, InitFields(X=X, T=T, u=u, P=0.4 / 20.8), steps=50)
+
+
+@pytest.mark.parametrize("bc_x", [0, 1])
+@pytest.mark.parametrize("mode,steps,tol", [("fp64", 50, 1e-10), ("mixed", 100, 1e-4), ("mixed_fast", 100, 1e-4)])
+def test_binary_mixture_two_species(orc, lbm, bc_x, mode, steps, tol):
+    prob = _binary_problem(bc_x)
+    s, o = _run_pair(orc, lbm, prob, steps, _mode(lbm, mode))
+    gpu, ref = _gpu_moments(s, lbm), _oracle_moments(o)
+    if mode == "fp64":
+        _compare(gpu, ref, tol)
+    else:
+        err = _mixed_errors(gpu, ref, 2)
+        assert max(err.values()) <= tol, err
