@@ -458,6 +458,47 @@ def run_flames(args):
         dist.destroy_process_group()
 
 
+def run_accuracy(args):
+    """Field error of the mixed modes against the double GPU step on the
+    whole benchmark lattice after K steps: max |F - F_fp64| / max |F_fp64|
+    for T and for each Y_a (the 1e-4 bar of the mixed-precision design)."""
+    import torch
+    import workload as w
+    from paper_2101_01702_gb300 import build
+    build.build()
+    from paper_2101_01702_gb300 import lbm
+
+    n = args.size
+    prob = w.sphere3d_problem(n=n, radius=20.0 * n / 256.0)
+    K = args.accuracy_steps
+    mask = lbm.LBM_F_T | lbm.LBM_F_Y
+
+    def run(precision):
+        s = lbm.Solver.from_problem(prob, precision=precision)
+        t0 = time.perf_counter()
+        s.step(K)
+        dt = time.perf_counter() - t0
+        m = s.moments(mask, device=True)
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        return m, dt
+
+    ref, t_ref = run(lbm.LBM_FP64)
+    out = {"metric": f"relative field error after {K} steps against the double GPU step",
+           "config": {"workload": f"sphere3d_{n}^3_M9", "nodes": prob.lattice.n_nodes, "steps": K},
+           "fp64_seconds": t_ref}
+    for name, precision in (("mixed", lbm.LBM_MIXED), ("mixed_fast", lbm.LBM_MIXED_FAST)):
+        m, dt = run(precision)
+        errT = float(((m["T"] - ref["T"]).abs().max() / ref["T"].abs().max()).item())
+        errY = [float(((m["Y"][a] - ref["Y"][a]).abs().max() / ref["Y"][a].abs().max()).item())
+                for a in range(prob.species.M)]
+        out[name] = {"T": errT, "Y": errY, "max": max([errT] + errY), "seconds": dt}
+        del m
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,11 +512,15 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
+    ap.add_argument("--accuracy-steps", type=int, default=0,
+                    help="instead of timing: field error of the mixed modes against double after this many steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.accuracy_steps > 0:
+        run_accuracy(args)
     elif args.workload == "flames48":
         run_flames(args)
     else:

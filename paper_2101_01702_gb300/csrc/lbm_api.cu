@@ -585,7 +585,7 @@ const char *lbm_strerror(int s)
     case LBM_ERR_NEWTON: return "temperature iteration did not converge";
     case LBM_ERR_NONFINITE: return "non-finite density, energy or population";
     case LBM_ERR_NEGATIVE: return "negative species density";
-    case LBM_ERR_PIVOT: return "zero pivot in the Stefan-Maxwell solve";
+    case LBM_ERR_PIVOT: return "non-finite pivot in the Stefan-Maxwell solve";
     case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown status";
     }

@@ -902,9 +902,14 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
                 for (int j = 0; j < k; ++j) sacc = fma(-Ln[i][j], tk[j], sacc);
                 Ln[i][k] = sacc;
             }
+            // D_k = Y_k times the pivot of the unscaled system, which is
+            // diagonally dominant: negative where a trace species has dipped
+            // to a rounding-level negative density, zero only for an absent
+            // species (Y_k = 0), whose row and column vanish and whose
+            // diffusion velocity is multiplied by Y_k = 0 wherever it is used.
             D[k] = Ln[k][k];
-            if (!(D[k] > (SReal)0)) flag(a.status, LBMK_BIT_PIVOT);
-            Dinv[k] = (SReal)1 / D[k];
+            if (!isfinite(D[k])) flag(a.status, LBMK_BIT_PIVOT);
+            Dinv[k] = D[k] != (SReal)0 ? (SReal)1 / D[k] : (SReal)0;
 #pragma unroll
             for (int i = k + 1; i < M; ++i) Ln[i][k] *= Dinv[k];
         }

@@ -214,3 +214,32 @@ def test_binary_mixture_two_species(orc, lbm, bc_x, mode, steps, tol):
     else:
         err = _mixed_errors(gpu, ref, 2)
         assert max(err.values()) <= tol, err
+
+
+@pytest.fixture(scope="module")
+def oracle_sphere64_r5(orc):
+    """The 64^3 expanding flame with a radius-5 kernel: after its second step
+    the oracle has nodes with slightly negative H mass fraction (about
+    -3.5e-14, a rounding-level undershoot well inside the -1e-10 rho band),
+    which the next step's Stefan-Maxwell solve must accept."""
+    prob = w.sphere3d_problem(n=64, radius=5.0)
+    o = orc.Oracle.from_problem(prob)
+    assert o.step(2) == 0
+    m2 = o.moments()
+    assert (m2["rho_a"] < 0).any()
+    assert o.step(4) == 0
+    return prob, o.moments()
+
+
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-10), ("mixed", 1e-4), ("mixed_fast", 1e-4)])
+def test_negative_trace_density_passes_through_the_solve(oracle_sphere64_r5, lbm, mode, tol):
+    prob, ref = oracle_sphere64_r5
+    s = lbm.Solver.from_problem(prob, precision=_mode(lbm, mode))
+    assert s.step(6, check=False) == lbm.LBM_OK
+    gpu = _gpu_moments(s, lbm)
+    s.close()
+    if mode == "fp64":
+        _compare(gpu, _fields(ref), tol)
+    else:
+        err = _mixed_errors(gpu, _fields(ref), 9)
+        assert max(err.values()) <= tol, err
