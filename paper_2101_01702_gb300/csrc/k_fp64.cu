@@ -45,6 +45,13 @@ int step_fp64(const StepArgs &a, cudaEvent_t *ev)
 #undef CALL
 }
 
+int ref_stats_fp64(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out)
+{
+#define CALL(M_) run_ref_stats<M_>(a, X, T, P, scratch, out)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 int moments_fp64(const StepArgs &a, unsigned mask, double *out)
 {
 #define CALL(M_) run_moments<M_>(a, mask, out)

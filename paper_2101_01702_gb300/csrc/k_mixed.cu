@@ -24,6 +24,13 @@ int step_mixed(const StepArgs &a, cudaEvent_t *ev)
 #undef CALL
 }
 
+int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out)
+{
+#define CALL(M_) run_ref_stats<M_>(a, X, T, P, scratch, out)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 int moments_mixed(const StepArgs &a, unsigned mask, double *out)
 {
 #define CALL(M_) run_moments<M_>(a, mask, out)

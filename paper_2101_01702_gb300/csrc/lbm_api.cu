@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/lbm.h"
@@ -53,9 +54,10 @@ bool valid_precision(int precision) { return precision == LBM_FP64 || is_mixed(p
 size_t store_size(int precision) { return is_mixed(precision) ? sizeof(float) : sizeof(double); }
 
 const lbmk::PrecisionOps kOps[3] = {
-    {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64},
-    {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed},
-    {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast},
+    {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64},
+    {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed},
+    {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
+     lbmk::ref_stats_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -173,33 +175,21 @@ double psi_host(int c, double zeta) { return c == 0 ? 1.0 - zeta : 0.5 * zeta; }
 // at the mean initial temperature and at the smallest initial density of
 // that set, so that the stored deviations of positive populations stay
 // non-negative and trace species keep float's relative precision.
-void choose_references(MechConst &mc, int M, const double *X, const double *T, double P, size_t N)
+// st: the statistics of the initial state from lbmk::ref_stats_* (min
+// rho_a (M), min rho, sum rho_a (M), sum rho, sum T) over N nodes.
+void references_from_stats(MechConst &mc, int M, const double *st, size_t N)
 {
-    double rho_min[LBMK_MAXM], rho_m[LBMK_MAXM] = {0}, T_m = 0.0, rho_t = 0.0, rho_tmin = 1e300;
-    for (int a = 0; a < M; ++a) rho_min[a] = 1e300;
-    for (size_t n = 0; n < N; ++n) {
-        double m = 0.0;
-        for (int a = 0; a < M; ++a) m += X[(size_t)a * N + n] * mc.W[a];
-        const double rho = P * m / (mc.r_lat * T[n]);
-        for (int a = 0; a < M; ++a) {
-            const double ra = rho * X[(size_t)a * N + n] * mc.W[a] / m;
-            rho_m[a] += ra;
-            if (ra < rho_min[a]) rho_min[a] = ra;
-        }
-        T_m += T[n];
-        rho_t += rho;
-        if (rho < rho_tmin) rho_tmin = rho;
-    }
-    T_m /= (double)N;
-    rho_t /= (double)N;
+    const double rho_tmin = st[M];
+    const double rho_t = st[2 * M + 1] / (double)N;
+    const double T_m = st[2 * M + 2] / (double)N;
     double inv_m = 0.0;
-    for (int a = 0; a < M; ++a) inv_m += rho_m[a] / (double)N / rho_t / mc.W[a];
+    for (int a = 0; a < M; ++a) inv_m += st[M + 1 + a] / (double)N / rho_t / mc.W[a];
     const double Rm = mc.r_lat * inv_m;
     for (int s = 0; s < M; ++s)
         for (int i = 0; i < LBMK_Q; ++i) {
             const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
             const double zeta = (s < M - 1 ? mc.Ra[s] : Rm) * T_m;
-            const double r = s < M - 1 ? rho_min[s] : rho_tmin;
+            const double r = s < M - 1 ? st[s] : rho_tmin;
             const double v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
             mc.ref[s][i] = i == 13 ? 0.0f : (float)v;     // rest populations are stored in double
         }
@@ -313,33 +303,13 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
     const bool dX = is_device_ptr(X), dT = is_device_ptr(T), du = u ? is_device_ptr(u) : dX;
     if (dX != dT || dX != du) return LBM_ERR_ARG;     // all host or all device
     int st = LBM_OK;
-    if (is_mixed(c->lat.precision) && !c->refs_fixed) {
-        // rest states from the mean initial state
-        const double *hX = X, *hT = T;
-        double *tmpX = nullptr, *tmpT = nullptr;
-        if (dX) {
-            tmpX = (double *)malloc(M * N * sizeof(double));
-            tmpT = (double *)malloc(N * sizeof(double));
-            if (!tmpX || !tmpT) { free(tmpX); free(tmpT); return LBM_ERR_ARG; }
-            st = check_cuda(cudaMemcpy(tmpX, X, M * N * sizeof(double), cudaMemcpyDeviceToHost));
-            if (st == LBM_OK) st = check_cuda(cudaMemcpy(tmpT, T, N * sizeof(double), cudaMemcpyDeviceToHost));
-            hX = tmpX;
-            hT = tmpT;
-        }
-        if (st == LBM_OK) {
-            choose_references(c->mc, c->M, hX, hT, P, N);
-            st = reslot(c);
-        }
-        free(tmpX);
-        free(tmpT);
-        if (st != LBM_OK) return st;
-    }
+    // The second population buffer is free until the first step: host fields
+    // are staged there, followed by the scratch of the reference statistics.
+    double *stage = (double *)c->buf[1 - c->cur];
+    const size_t stage_doubles = dX ? 0 : (M + 4) * N;
+    if (stage_doubles * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
     const double *dXp = X, *dTp = T, *dup = u;
     if (!dX) {
-        // stage host fields through the second population buffer
-        double *stage = (double *)c->buf[1 - c->cur];
-        const size_t need = (M + 4) * N * sizeof(double);
-        if (need > c->pop_bytes) return LBM_ERR_ARG;
         st = check_cuda(cudaMemcpyAsync(stage, X, M * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         if (st == LBM_OK)
             st = check_cuda(cudaMemcpyAsync(stage + M * N, T, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -350,6 +320,25 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
         dXp = stage;
         dTp = stage + M * N;
         dup = u ? stage + (M + 1) * N : nullptr;
+    }
+    if (is_mixed(c->lat.precision) && !c->refs_fixed) {
+        // rest references from statistics of the initial state, reduced on
+        // the GPU in a fixed order
+        const size_t len = 2 * M + 3;
+        const size_t nb = std::min<size_t>(LBMK_STAT_BLOCKS, (N + 255) / 256);
+        const size_t off = (stage_doubles + 31) & ~(size_t)31;
+        if ((off + (nb + 1) * len) * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+        double *scratch = stage + off, *dstat = scratch + nb * len;
+        if (ops(c->lat.precision).ref_stats(args_of(c), dXp, dTp, P, scratch, dstat)) return LBM_ERR_CUDA;
+        double hstat[2 * LBMK_MAXM + 3];
+        st = check_cuda(cudaMemcpyAsync(hstat, dstat, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
+        if (st != LBM_OK) return st;
+        for (size_t k = 0; k < len; ++k)
+            if (!isfinite(hstat[k])) return LBM_ERR_ARG;      // a non-finite or non-positive initial state
+        references_from_stats(c->mc, c->M, hstat, N);
+        st = reslot(c);
+        if (st != LBM_OK) return st;
     }
     StepArgs a = args_of(c);
     a.dst = c->buf[c->cur];

@@ -144,11 +144,21 @@ int moments_fp64(const StepArgs &a, unsigned mask, double *out);
 int moments_mixed(const StepArgs &a, unsigned mask, double *out);
 int moments_mixed_fast(const StepArgs &a, unsigned mask, double *out);
 
+// statistics of an initial state (X [M][N], T [N], pressure P; device) for
+// the rest references: out = {min rho_a (M), min rho, sum rho_a (M), sum rho,
+// sum T}; scratch holds LBMK_STAT_SCRATCH(M) doubles
+#define LBMK_STAT_BLOCKS 1024
+#define LBMK_STAT_SCRATCH(M_) (LBMK_STAT_BLOCKS * (2 * (M_) + 3))
+int ref_stats_fp64(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
+int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
+int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
+
 // The kernel unit of one storage/arithmetic precision.
 struct PrecisionOps {
     int (*upload)(int slot, const MechConst &mc, cudaStream_t s);
     int (*init)(const StepArgs &a, const double *X, const double *T, const double *u, double P);
     int (*step)(const StepArgs &a, cudaEvent_t *ev);
     int (*moments)(const StepArgs &a, unsigned mask, double *out);
+    int (*ref_stats)(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 };
 }  // namespace lbmk

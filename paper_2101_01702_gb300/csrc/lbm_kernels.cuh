@@ -1419,6 +1419,119 @@ int run_init(const StepArgs &a, const double *X, const double *T, const double *
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------
+// Statistics of an initial state from which the mixed modes choose their
+// rest references: per node rho = P m / (r_lat T) (m = sum_a X_a W_a) and
+// rho_a = rho X_a W_a / m; over the lattice the minima of rho_a and rho and
+// the sums of rho_a, rho and T.  Record of 2M+3 doubles: min rho_a (M),
+// min rho, sum rho_a (M), sum rho, sum T.  Two passes with a fixed
+// reduction order (LBMK_STAT_BLOCKS partial records, then one block), so
+// that the result -- and every state that depends on it -- is the same
+// from run to run.
+// ---------------------------------------------------------------------
+constexpr int LBMK_STAT_THREADS = 256;
+
+__host__ __device__ constexpr int stat_len(int M) { return 2 * M + 3; }
+
+template <int M>
+__device__ __forceinline__ void stat_combine(double *acc, const double *o)
+{
+#pragma unroll
+    for (int k = 0; k <= M; ++k) acc[k] = fmin(acc[k], o[k]);
+#pragma unroll
+    for (int k = M + 1; k < stat_len(M); ++k) acc[k] += o[k];
+}
+
+template <int M>
+__device__ __forceinline__ void stat_identity(double *acc)
+{
+#pragma unroll
+    for (int k = 0; k <= M; ++k) acc[k] = INFINITY;
+#pragma unroll
+    for (int k = M + 1; k < stat_len(M); ++k) acc[k] = 0.0;
+}
+
+// Tree reduction of the block's records in shared memory (fixed order);
+// thread 0 leaves the block's record in sh[0 .. stat_len(M)).
+template <int M>
+__device__ __forceinline__ void stat_block_reduce(double *acc, double *sh)
+{
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < stat_len(M); ++k) sh[k * LBMK_STAT_THREADS + t] = acc[k];
+    __syncthreads();
+    for (int w = LBMK_STAT_THREADS / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            double o[stat_len(M)];
+#pragma unroll
+            for (int k = 0; k < stat_len(M); ++k) o[k] = sh[k * LBMK_STAT_THREADS + t + w];
+            stat_combine<M>(acc, o);
+#pragma unroll
+            for (int k = 0; k < stat_len(M); ++k) sh[k * LBMK_STAT_THREADS + t] = acc[k];
+        }
+        __syncthreads();
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_STAT_THREADS) k_stat_partial(StepArgs a, const double *X, const double *T,
+                                                                     double P, double *partial)
+{
+    __shared__ double sh[stat_len(M) * LBMK_STAT_THREADS];
+    const MechConst &mc = c_mech[a.slot];
+    double acc[stat_len(M)];
+    stat_identity<M>(acc);
+    for (int n = blockIdx.x * LBMK_STAT_THREADS + threadIdx.x; n < a.N; n += gridDim.x * LBMK_STAT_THREADS) {
+        double m = 0.0;
+#pragma unroll
+        for (int s = 0; s < M; ++s) m += X[(size_t)s * a.N + n] * mc.W[s];
+        const double Tn = T[n];
+        const double rho = P * m / (mc.r_lat * Tn);
+        double o[stat_len(M)];
+#pragma unroll
+        for (int s = 0; s < M; ++s) {
+            const double ra = rho * X[(size_t)s * a.N + n] * mc.W[s] / m;
+            o[s] = ra;
+            o[M + 1 + s] = ra;
+        }
+        o[M] = rho;
+        o[2 * M + 1] = rho;
+        o[2 * M + 2] = Tn;
+        stat_combine<M>(acc, o);
+    }
+    stat_block_reduce<M>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < stat_len(M); ++k) partial[(size_t)k * gridDim.x + blockIdx.x] = sh[k * LBMK_STAT_THREADS];
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_STAT_THREADS) k_stat_final(const double *partial, int nblocks, double *out)
+{
+    __shared__ double sh[stat_len(M) * LBMK_STAT_THREADS];
+    double acc[stat_len(M)];
+    stat_identity<M>(acc);
+    for (int b = threadIdx.x; b < nblocks; b += LBMK_STAT_THREADS) {
+        double o[stat_len(M)];
+#pragma unroll
+        for (int k = 0; k < stat_len(M); ++k) o[k] = partial[(size_t)k * nblocks + b];
+        stat_combine<M>(acc, o);
+    }
+    stat_block_reduce<M>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < stat_len(M); ++k) out[k] = sh[k * LBMK_STAT_THREADS];
+}
+
+// scratch: device, at least LBMK_STAT_BLOCKS * (2M+3) doubles; out: device, 2M+3 doubles.
+template <int M>
+int run_ref_stats(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out)
+{
+    const int nb = (int)std::min<long long>(LBMK_STAT_BLOCKS, ((long long)a.N + LBMK_STAT_THREADS - 1) /
+                                                                  LBMK_STAT_THREADS);
+    k_stat_partial<M><<<nb, LBMK_STAT_THREADS, 0, a.stream>>>(a, X, T, P, scratch);
+    k_stat_final<M><<<1, LBMK_STAT_THREADS, 0, a.stream>>>(scratch, nb, out);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace
 
 #define LBMK_DISPATCH(M_, CALL)                     \
