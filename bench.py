@@ -45,9 +45,9 @@ FP64_FLOPS_PER_NODE = {
     "fp64": {"k_pre": 2859.4, "k_chem": 1236.0, "k_step_g": 737.0, "k_step": 12534.0},
 }
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2961.1, "k_chem": 64.8, "k_step_g": 600.2, "k_step": 2402.6},
-    "mixed_fast": {"k_pre": 2202.6, "k_chem": 64.5, "k_step_g": 600.2, "k_step": 2402.2},
-    "fp64": {"k_pre": 3409.6, "k_chem": 138.2, "k_step_g": 699.8, "k_step": 4464.2},
+    "mixed": {"k_pre": 2945.6, "k_chem": 64.5, "k_step_g": 600.4, "k_step": 2402.8},
+    "mixed_fast": {"k_pre": 2244.4, "k_chem": 64.5, "k_step_g": 600.1, "k_step": 2402.4},
+    "fp64": {"k_pre": 3410.1, "k_chem": 138.2, "k_step_g": 699.9, "k_step": 4464.3},
 }
 
 
