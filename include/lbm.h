@@ -196,6 +196,29 @@ int lbm_step_async(lbm_ctx *ctx, int n);
  * stream (LBM_ERR_UNSUPPORTED).  Errors surface at lbm_sync(). */
 int lbm_step_graph(lbm_ctx *ctx, int n);
 
+/* Autotuner of the launch shapes (the paper has no counterpart): times
+ * each kernel of the step on the context's current state with every
+ * candidate block size -- 64 or 128 threads for the moment and species-
+ * collision kernels, whose register budgets are set for 128, and 64, 128
+ * or 256 for the production-rate, gradient and energy-collision kernels --
+ * over `trials` launches (1..1000) after two untimed ones, and keeps the
+ * fastest for every later step of this context.  The state is left as it
+ * was (the kernels write only the per-node record and the other buffer;
+ * the temperature row, the next Newton start, is restored), so results
+ * are bit for bit those of the untuned context.  Allocates and frees one
+ * temporary row of N doubles.  block_out (NULL or 6 ints) receives the
+ * chosen blocks in launch order: ghost nodes, moments, production rates,
+ * gradients, energy collision, species/mixture collision.  Waits for the
+ * stream; returns like lbm_sync. */
+int lbm_autotune(lbm_ctx *ctx, int trials, int *block_out);
+
+/* Sets the block sizes of the six kernels directly (for instance a choice
+ * lbm_autotune made in an earlier run): blocks[6] in the order of
+ * block_out above, each 64, 128 or 256, at most 128 for the moment and
+ * species-collision kernels, and 128 for the ghost-node kernel; else
+ * LBM_ERR_ARG.  Results do not depend on the choice. */
+int lbm_set_blocks(lbm_ctx *ctx, const int *blocks);
+
 /* lbm_step_async with CUDA events recorded on the stream between the
  * kernels of each step (all steps enqueued back to back, one wait at the
  * end).  phase_ms must hold LBM_PHASES + 1 doubles: phase_ms[0..5] receive

@@ -90,6 +90,7 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     a.nseg = 0;
     a.xseg = nullptr;
     a.segs = nullptr;
+    for (int k = 0; k < LBMK_NKERNELS; ++k) a.bs[k] = LBMK_BLOCK;
     a.src = pop_in;
     a.dst = pop_out;
     a.status = (unsigned *)scratch;

@@ -31,6 +31,13 @@ int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double 
 #undef CALL
 }
 
+int launch_one_mixed(const StepArgs &a, int kernel)
+{
+#define CALL(M_) launch_one<M_>(a, kernel)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 int moments_mixed(const StepArgs &a, unsigned mask, double *out)
 {
 #define CALL(M_) run_moments<M_>(a, mask, out)

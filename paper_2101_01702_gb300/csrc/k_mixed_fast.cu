@@ -32,6 +32,13 @@ int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, do
 #undef CALL
 }
 
+int launch_one_mixed_fast(const StepArgs &a, int kernel)
+{
+#define CALL(M_) launch_one<M_>(a, kernel)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 int moments_mixed_fast(const StepArgs &a, unsigned mask, double *out)
 {
 #define CALL(M_) run_moments<M_>(a, mask, out)

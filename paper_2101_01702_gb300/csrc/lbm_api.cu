@@ -1,9 +1,10 @@
 // C ABI of the reactive-mixture lattice Boltzmann library (include/lbm.h).
 //
 // Host side only: argument validation, packing of the species and mechanism
-// tables into the constant-memory record the kernels read, buffer binding,
-// the A/B swap of the population buffers, and status reporting.  Every step
-// of the numerical method runs in the kernels of k_fp64.cu / k_mixed.cu.
+// tables into the constant-memory record the kernels read (slots shared by
+// identical tables), buffer binding, the A/B swap of the population buffers,
+// CUDA-graph replay, and status reporting.  Every step of the numerical
+// method runs in the kernels of k_fp64.cu, k_mixed.cu and k_mixed_fast.cu.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -32,6 +33,7 @@ struct lbm_ctx {
     cudaGraphExec_t graph;   // two captured steps (lbm_step_graph), or null
     int graph_cur;           // value of cur the graph starts from
     bool refs_fixed;         // rest references set by lbm_set_references
+    int bs[LBMK_NKERNELS];   // threads per block of each kernel (lbm_autotune)
 };
 
 namespace {
@@ -54,10 +56,12 @@ bool valid_precision(int precision) { return precision == LBM_FP64 || is_mixed(p
 size_t store_size(int precision) { return is_mixed(precision) ? sizeof(float) : sizeof(double); }
 
 const lbmk::PrecisionOps kOps[3] = {
-    {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64},
-    {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed},
+    {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64,
+     lbmk::launch_one_fp64},
+    {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed,
+     lbmk::launch_one_mixed},
     {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
-     lbmk::ref_stats_mixed_fast},
+     lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -156,6 +160,7 @@ StepArgs args_of(const lbm_ctx *c)
     a.nz = c->lat.nz;
     a.N = c->N;
     a.bc_x = c->lat.bc_x;
+    for (int k = 0; k < LBMK_NKERNELS; ++k) a.bs[k] = c->bs[k];
     a.nseg = c->nseg;
     a.xseg = c->xseg;
     a.segs = c->segs;
@@ -267,6 +272,7 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     c->pop_bytes = need_pop;
     c->mc = mc;
     c->lat.seg_nx = nullptr;     // read here only
+    for (int k = 0; k < LBMK_NKERNELS; ++k) c->bs[k] = LBMK_BLOCK;
     int st = check_cuda(cudaMalloc((void **)&c->status, 16));
     if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
     if (st == LBM_OK && lat->nseg > 1) {
@@ -398,6 +404,100 @@ int lbm_step_graph(lbm_ctx *c, int n)
     for (; left >= 2; left -= 2)          // two steps leave cur where it was
         if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return LBM_ERR_CUDA;
     return left == 1 ? lbm_step_async(c, 1) : LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx *c, int trials, int *block_out)
+{
+    if (!c || trials < 1 || trials > 1000) return LBM_ERR_ARG;
+    int st = lbm_sync(c);
+    if (st != LBM_OK) return st;
+    // Candidate blocks per kernel: k_pre and k_step carry register caps for
+    // 128-thread blocks, so at most 128; the others up to LBMK_MAXBLOCK.
+    static const int cand[3] = {64, 128, 256};
+    const int maxbs[LBMK_NKERNELS] = {LBMK_BLOCK, LBMK_BLOCK, LBMK_MAXBLOCK, LBMK_MAXBLOCK, LBMK_MAXBLOCK,
+                                      LBMK_BLOCK};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return LBM_ERR_CUDA;
+    }
+    const lbmk::PrecisionOps &op = ops(c->lat.precision);
+    // Every kernel of the step reads the current state (and the record the
+    // earlier kernels write from it) and writes only the record and the other
+    // buffer, so repeating any of them leaves the state as it was -- except
+    // the temperature row, the Newton start of the next step, which repeated
+    // iterations may move by a rounding: it is kept aside and put back.
+    double *t_keep = nullptr;
+    const size_t tbytes = (size_t)c->N * sizeof(double);
+    if (cudaMalloc((void **)&t_keep, tbytes) != cudaSuccess ||
+        cudaMemcpyAsync(t_keep, c->macro + (size_t)DR_T * c->N, tbytes, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess) {
+        if (t_keep) cudaFree(t_keep);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return LBM_ERR_CUDA;
+    }
+    for (int k = 0; k < LBMK_NKERNELS && st == LBM_OK; ++k) {
+        StepArgs a = args_of(c);
+        if (op.launch_one(a, k)) { st = LBM_ERR_CUDA; break; }     // the kernel's inputs, at the current choice
+        if (k == LBMK_K_GHOST) continue;
+        float best = 0.f;
+        for (int j = 0; j < 3 && st == LBM_OK; ++j) {
+            if (cand[j] > maxbs[k]) continue;
+            a.bs[k] = cand[j];
+            for (int w = 0; w < 2 + trials && st == LBM_OK; ++w) {   // 2 untimed, then trials timed
+                if (w == 2 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
+                if (op.launch_one(a, k)) st = LBM_ERR_CUDA;
+            }
+            if (st != LBM_OK) break;
+            float ms = 0.f;
+            if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = LBM_ERR_CUDA;
+                break;
+            }
+            if (best == 0.f || ms < best) {
+                best = ms;
+                c->bs[k] = cand[j];
+            }
+        }
+        a = args_of(c);
+        if (st == LBM_OK && op.launch_one(a, k)) st = LBM_ERR_CUDA;   // leave its outputs from the choice
+    }
+    if (cudaMemcpyAsync(c->macro + (size_t)DR_T * c->N, t_keep, tbytes, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        st = LBM_ERR_CUDA;
+    cudaFree(t_keep);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (c->graph) {                      // captured with the previous blocks
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (block_out)
+        for (int k = 0; k < LBMK_NKERNELS; ++k) block_out[k] = c->bs[k];
+    if (st != LBM_OK) return st;
+    return lbm_sync(c);
+}
+
+int lbm_set_blocks(lbm_ctx *c, const int *blocks)
+{
+    if (!c || !blocks) return LBM_ERR_ARG;
+    const int maxbs[LBMK_NKERNELS] = {LBMK_BLOCK, LBMK_BLOCK, LBMK_MAXBLOCK, LBMK_MAXBLOCK, LBMK_MAXBLOCK,
+                                      LBMK_BLOCK};
+    for (int k = 0; k < LBMK_NKERNELS; ++k) {
+        const int b = blocks[k];
+        if ((b != 64 && b != 128 && b != 256) || b > maxbs[k] || (k == LBMK_K_GHOST && b != LBMK_BLOCK))
+            return LBM_ERR_ARG;
+    }
+    for (int k = 0; k < LBMK_NKERNELS; ++k) c->bs[k] = blocks[k];
+    if (c->graph) {                      // captured with the previous blocks
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return LBM_OK;
 }
 
 int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)

@@ -105,8 +105,16 @@ struct MechConst {
     float ref[LBMK_MAXS][LBMK_Q];
 };
 
+#define LBMK_BLOCK 128      // default block; the block of k_pre and k_step is at most this
+#define LBMK_MAXBLOCK 256   // largest block of the kernels tuned up to it (k_chem, k_grad, k_step_g)
+
+// The kernels of one step, in launch order (timing phases and autotuned
+// block sizes are indexed alike).
+enum { LBMK_K_GHOST = 0, LBMK_K_PRE, LBMK_K_CHEM, LBMK_K_GRAD, LBMK_K_STEPG, LBMK_K_STEP, LBMK_NKERNELS };
+
 struct StepArgs {
     int slot, M, nx, ny, nz, N, bc_x;
+    int bs[LBMK_NKERNELS];   // threads per block of each kernel
     // Lattices side by side in x (nseg >= 2): per x coordinate its lattice's
     // x range and index {x0, x1, k, 0}; per lattice its range {x0, x1}.
     // Null for one lattice (x0 = 0, x1 = nx, k = 0).
@@ -153,6 +161,11 @@ int ref_stats_fp64(const StepArgs &a, const double *X, const double *T, double P
 int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 
+// one kernel of the step (LBMK_K_*) with the block size a.bs[kernel]
+int launch_one_fp64(const StepArgs &a, int kernel);
+int launch_one_mixed(const StepArgs &a, int kernel);
+int launch_one_mixed_fast(const StepArgs &a, int kernel);
+
 // The kernel unit of one storage/arithmetic precision.
 struct PrecisionOps {
     int (*upload)(int slot, const MechConst &mc, cudaStream_t s);
@@ -160,5 +173,6 @@ struct PrecisionOps {
     int (*step)(const StepArgs &a, cudaEvent_t *ev);
     int (*moments)(const StepArgs &a, unsigned mask, double *out);
     int (*ref_stats)(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
+    int (*launch_one)(const StepArgs &a, int kernel);
 };
 }  // namespace lbmk

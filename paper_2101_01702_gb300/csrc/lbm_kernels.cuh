@@ -55,7 +55,6 @@ typedef double WReal;
 #define INVWWD_S(a_, b_) (mc.inv_WWD[a_][b_])
 #endif
 
-#define LBMK_BLOCK 128
 // Minimum resident blocks per SM asked of the compiler for the two large
 // kernels (register budget 65536 / (LBMK_BLOCK * minB)).  Measured on the
 // 256^3 nine-species lattice: the moment pass runs fastest at 5 blocks in
@@ -675,11 +674,11 @@ __device__ __forceinline__ double exp_rate(double x)
 }
 
 // Molar production rates sum_k (nu''_ak - nu'_ak) q_k at temperature T and
-// concentrations conc, left in sh_w[a * LBMK_BLOCK + t]; sh_act and sh_g
-// are this thread's scratch columns.
+// concentrations conc, left in sh_w[a * stride + t]; sh_act and sh_g are
+// this thread's scratch columns (stride: the block's thread count).
 template <int M>
 __device__ __forceinline__ void molar_production(const MechConst &mc, double T, const double *conc, double *sh_act,
-                                                 double *sh_g, WReal *sh_w, int t)
+                                                 double *sh_g, WReal *sh_w, int t, int stride)
 {
     const double invT = 1.0 / T, lnT = log(T);
     const double lnTr = lnT - mc.log_T_ref;
@@ -689,25 +688,25 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
         const double *gc = mc.gco[s];
         const double g = fma(gc[0], om_lnT,
                              fma(fma(fma(fma(gc[4], T, gc[3]), T, gc[2]), T, gc[1]), T, fma(gc[5], invT, gc[6])));
-        sh_g[s * LBMK_BLOCK + t] = g;
-        sh_act[s * LBMK_BLOCK + t] = conc[s] * exp_rate(g);
-        sh_w[s * LBMK_BLOCK + t] = 0;
+        sh_g[s * stride + t] = g;
+        sh_act[s * stride + t] = conc[s] * exp_rate(g);
+        sh_w[s * stride + t] = 0;
     }
     const double c0 = mc.P0_over_r * invT, ic0 = T / mc.P0_over_r;   // P0/(r T) and its inverse
     for (int k = 0; k < mc.R; ++k) {
         const int nr = mc.nreac[k], np = mc.nprod[k];     // nr >= 1 (checked at packing)
-        const int s0 = mc.reac[k][0] * LBMK_BLOCK + t;
+        const int s0 = mc.reac[k][0] * stride + t;
         double arg = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k])) - sh_g[s0];
         double pf = sh_act[s0];
         for (int j = 1; j < nr; ++j) {
-            const int sidx = mc.reac[k][j] * LBMK_BLOCK + t;
+            const int sidx = mc.reac[k][j] * stride + t;
             arg -= sh_g[sidx];
             pf *= sh_act[sidx];
         }
         double q = pf;
         if (mc.rev[k]) {
-            double pr = np > 0 ? sh_act[mc.prod[k][0] * LBMK_BLOCK + t] : 1.0;
-            for (int j = 1; j < np; ++j) pr *= sh_act[mc.prod[k][j] * LBMK_BLOCK + t];
+            double pr = np > 0 ? sh_act[mc.prod[k][0] * stride + t] : 1.0;
+            for (int j = 1; j < np; ++j) pr *= sh_act[mc.prod[k][j] * stride + t];
             const int dn = mc.dn[k];
             for (int j = 0; j < dn; ++j) pr *= ic0;
             for (int j = 0; j < -dn; ++j) pr *= c0;
@@ -727,8 +726,8 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
             }
         }
         const WReal qr = (WReal)q;
-        for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * LBMK_BLOCK + t] -= qr;
-        for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * LBMK_BLOCK + t] += qr;
+        for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * stride + t] -= qr;
+        for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * stride + t] += qr;
     }
 }
 
@@ -784,7 +783,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mas
         double conc[M];
 #pragma unroll
         for (int s = 0; s < M; ++s) conc[s] = rho_a[s] * mc.invW[s];
-        molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, threadIdx.x);
+        molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, threadIdx.x, LBMK_BLOCK);
         for (int s = 0; s < M; ++s) out[(row + s) * N + n] = mc.W[s] * (double)sh_w[s * LBMK_BLOCK + threadIdx.x];
     }
 }
@@ -1017,12 +1016,18 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
 // ---------------------------------------------------------------------
 // Pass 1b: production rates of the record's state (molar_production).
 // ---------------------------------------------------------------------
+// Shared memory of k_chem for a block of bs threads.
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
+constexpr size_t chem_smem(int bs) { return (size_t)M * bs * (2 * sizeof(double) + sizeof(WReal)); }
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_MAXBLOCK) k_chem(StepArgs a)
 {
-    __shared__ double sh_act[M * LBMK_BLOCK];   // c_a exp(g_a / R_U T)
-    __shared__ double sh_g[M * LBMK_BLOCK];     // g_a / R_U T
-    __shared__ WReal sh_w[M * LBMK_BLOCK];      // molar production
+    extern __shared__ double sh_chem[];
+    const int bs = blockDim.x;
+    double *sh_act = sh_chem;                                   // c_a exp(g_a / R_U T)
+    double *sh_g = sh_chem + (size_t)M * bs;                    // g_a / R_U T
+    WReal *sh_w = reinterpret_cast<WReal *>(sh_chem + (size_t)2 * M * bs);   // molar production
     const MechConst &mc = c_mech[a.slot];
     const int t = threadIdx.x;
     const int n = blockIdx.x * blockDim.x + t;
@@ -1035,9 +1040,9 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
     double conc[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) conc[s] = rho * (double)R[(size_t)(rr.y + s) * N + n] * mc.invW[s];
-    molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, t);
+    molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, t, bs);
 #pragma unroll
-    for (int s = 0; s < M; ++s) R[(size_t)(rr.wd + s) * N + n] = (Real)(mc.W[s] * sh_w[s * LBMK_BLOCK + t]);
+    for (int s = 0; s < M; ++s) R[(size_t)(rr.wd + s) * N + n] = (Real)(mc.W[s] * sh_w[s * bs + t]);
 }
 
 // ---------------------------------------------------------------------
@@ -1045,7 +1050,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_chem(StepArgs a)
 // gradient d_alpha phi = (1/theta) sum_i w_i c_ia phi(x + c_i).
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
+__global__ void __launch_bounds__(LBMK_MAXBLOCK) k_grad(StepArgs a)
 {
     Node nd;
     if (!node_of(nd, a)) return;
@@ -1081,7 +1086,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_grad(StepArgs a)
 // R = R^eq - rho E theta I (Eq. (gieq) expanded in c_i).  Double precision.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_step_g(StepArgs a)
+__global__ void __launch_bounds__(LBMK_MAXBLOCK) k_step_g(StepArgs a)
 {
     Node nd;
     if (!node_of(nd, a)) return;
@@ -1377,27 +1382,56 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 // ---------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------
-inline dim3 grid_for(int n) { return dim3((unsigned)((n + LBMK_BLOCK - 1) / LBMK_BLOCK)); }
+inline dim3 grid_for(int n, int bs = LBMK_BLOCK) { return dim3((unsigned)((n + bs - 1) / bs)); }
+
+// Launch of one kernel of the step with the context's block size for it
+// (LBMK_K_*; the autotuner times them one at a time).
+template <int M>
+int launch_one(const StepArgs &a, int k)
+{
+    const int bs = a.bs[k];
+    switch (k) {
+    case LBMK_K_GHOST:
+        if (a.bc_x == 1) {
+            const int plane = a.ny * a.nz;
+            k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
+        }
+        break;
+    case LBMK_K_PRE: k_pre<M><<<grid_for(a.N, bs), bs, 0, a.stream>>>(a); break;
+    case LBMK_K_CHEM: {
+        // blocks needing more than 48 KB of dynamic shared memory opt in,
+        // once per device (only tuned block sizes do; the default never)
+        if (chem_smem<M>(bs) > 48 * 1024) {
+            static unsigned long long opted = 0;     // bit d: device d has opted in
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+            if (!(opted >> dev & 1ull)) {
+                const cudaError_t e = cudaFuncSetAttribute(k_chem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)chem_smem<M>(LBMK_MAXBLOCK));
+                if (e != cudaSuccess) return (int)e;
+                opted |= 1ull << dev;
+            }
+        }
+        k_chem<M><<<grid_for(a.N, bs), bs, chem_smem<M>(bs), a.stream>>>(a);
+        break;
+    }
+    case LBMK_K_GRAD: k_grad<M><<<grid_for(a.N, bs), bs, 0, a.stream>>>(a); break;
+    case LBMK_K_STEPG: k_step_g<M><<<grid_for(a.N, bs), bs, 0, a.stream>>>(a); break;
+    case LBMK_K_STEP: k_step<M><<<grid_for(a.N, bs), bs, 0, a.stream>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
 
 template <int M>
 int run_step(const StepArgs &a, cudaEvent_t *ev)
 {
-    if (ev) cudaEventRecord(ev[0], a.stream);
-    if (a.bc_x == 1) {
-        const int plane = a.ny * a.nz;
-        k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
+    for (int k = 0; k < LBMK_NKERNELS; ++k) {
+        if (ev) cudaEventRecord(ev[k], a.stream);
+        const int e = launch_one<M>(a, k);
+        if (e) return e;
     }
-    if (ev) cudaEventRecord(ev[1], a.stream);
-    k_pre<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    if (ev) cudaEventRecord(ev[2], a.stream);
-    k_chem<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    if (ev) cudaEventRecord(ev[3], a.stream);
-    k_grad<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    if (ev) cudaEventRecord(ev[4], a.stream);
-    k_step_g<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    if (ev) cudaEventRecord(ev[5], a.stream);
-    k_step<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a);
-    if (ev) cudaEventRecord(ev[6], a.stream);
+    if (ev) cudaEventRecord(ev[LBMK_NKERNELS], a.stream);
     return (int)cudaGetLastError();
 }
 

@@ -73,6 +73,8 @@ _lib.lbm_init.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_do
 _lib.lbm_step.argtypes = [C.c_void_p, C.c_int]
 _lib.lbm_step_async.argtypes = [C.c_void_p, C.c_int]
 _lib.lbm_step_graph.argtypes = [C.c_void_p, C.c_int]
+_lib.lbm_autotune.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+_lib.lbm_set_blocks.argtypes = [C.c_void_p, C.c_void_p]
 _lib.lbm_get_references.argtypes = [C.c_void_p, C.c_void_p]
 _lib.lbm_set_references.argtypes = [C.c_void_p, C.c_void_p]
 _lib.lbm_sync.argtypes = [C.c_void_p]
@@ -93,7 +95,7 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
-            "lbm_set_references"]
+            "lbm_set_references", "lbm_autotune", "lbm_set_blocks"]
 
 
 def library_path() -> str:
@@ -143,6 +145,18 @@ def lbm_step_async(ctx, n: int) -> int:
 
 def lbm_step_graph(ctx, n: int) -> int:
     return _lib.lbm_step_graph(ctx, int(n))
+
+
+def lbm_autotune(ctx, trials: int, block_out: np.ndarray = None) -> int:
+    if block_out is not None:
+        assert block_out.dtype == np.int32 and block_out.size >= 6
+    return _lib.lbm_autotune(ctx, int(trials), block_out.ctypes.data if block_out is not None else None)
+
+
+def lbm_set_blocks(ctx, blocks) -> int:
+    b = np.ascontiguousarray(blocks, dtype=np.int32)
+    assert b.size == 6
+    return _lib.lbm_set_blocks(ctx, b.ctypes.data)
 
 
 def lbm_get_references(ctx, ref: np.ndarray) -> int:
@@ -305,6 +319,18 @@ class Solver:
 
     def step_async(self, n: int = 1):
         _check(lbm_step_async(self.ctx, n), "lbm_step_async")
+
+    def autotune(self, trials: int = 3) -> dict:
+        """Picks each kernel's block size by timing it on the current state
+        (results unchanged); returns the choice per kernel."""
+        bs = np.zeros(6, dtype=np.int32)
+        _check(lbm_autotune(self.ctx, trials, bs), "lbm_autotune")
+        return dict(zip(("ghost", "moments", "rates", "gradients", "energy_collision", "species_collision"),
+                        bs.tolist()))
+
+    def set_blocks(self, blocks):
+        """Block sizes of the six kernels in launch order (see autotune)."""
+        _check(lbm_set_blocks(self.ctx, blocks), "lbm_set_blocks")
 
     def references(self) -> np.ndarray:
         """Rest references of the mixed modes, float32 [M, 27]."""
