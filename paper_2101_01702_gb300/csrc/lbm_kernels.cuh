@@ -5,10 +5,13 @@
 //   LBMK_MIXED 1 : the moving populations of the species and mixture sets
 //                  stored as float deviations from per-set rest states and
 //                  collided in float; their rest populations and the whole
-//                  energy set in double (see pop_bytes_for).
-// In both units the moments, the temperature iteration (Eq. (temperature)),
+//                  energy set in double (see pop_bytes_for);
+//   LBMK_FAST 1  : (with LBMK_MIXED 1) also the relaxation rates, the
+//                  Stefan-Maxwell solve and the 2^f of the rate
+//                  exponentials in float (see SReal, WReal, exp_rate).
+// Otherwise the moments, the temperature iteration (Eq. (temperature)),
 // the Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
-// their equilibrium constants are double precision.
+// their equilibrium constants are double precision in every unit.
 //
 // One time step is six launches on one stream:
 //   k_ghost  x-face ghost nodes (Sec. 5a; only for non-periodic x)
@@ -28,6 +31,8 @@
 #pragma once
 
 #include <math.h>
+
+#include <algorithm>
 
 #include "lbm_internal.h"
 
