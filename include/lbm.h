@@ -43,6 +43,7 @@ enum {
     LBM_ERR_NONFINITE = -4,    /* a density, energy or population became NaN/Inf   */
     LBM_ERR_NEGATIVE = -5,     /* a species density fell below -1e-10 rho           */
     LBM_ERR_PIVOT = -6,        /* non-finite pivot in the Stefan-Maxwell elimination */
+    LBM_ERR_BOUNDS = -7,       /* checked builds: an index left its buffer (a bug)  */
     LBM_ERR_UNSUPPORTED = -8   /* valid request this build does not provide        */
 };
 

@@ -15,6 +15,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "liblbm.so"
+LIB_CHECKED = BUILD / "liblbm_checked.so"   # every geometry-derived index checked (tests)
 SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_mixed_fast.cu", "k_fixed_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -31,23 +32,28 @@ def _inputs():
         PKG.parent / "include" / "lbm.h"]
 
 
-def up_to_date() -> bool:
-    if not LIB.exists():
+def up_to_date(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return False
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     return all(p.stat().st_mtime <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> Path:
+    """Builds liblbm.so, or with checked=True liblbm_checked.so: the same
+    library compiled with LBMK_CHECKED=1, whose kernels check every index
+    they derive from the lattice geometry and report LBM_ERR_BOUNDS."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
     BUILD.mkdir(exist_ok=True)
     nvcc = _nvcc()
     tag = os.getpid()
 
     def compile_one(src: str):
-        obj = BUILD / f"{Path(src).stem}.{tag}.o"
-        cmd = [nvcc, *ARCH, *FLAGS, "-I", str(PKG.parent / "include"), "-c", str(CSRC / src), "-o", str(obj)]
+        obj = BUILD / f"{Path(src).stem}.{tag}{'.checked' if checked else ''}.o"
+        cmd = [nvcc, *ARCH, *FLAGS, *(["-DLBMK_CHECKED=1"] if checked else []), "-I", str(PKG.parent / "include"),
+               "-c", str(CSRC / src), "-o", str(obj)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,15 +65,15 @@ def build(force: bool = False, verbose: bool = False) -> Path:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = BUILD / f"liblbm.{tag}.so"
+    tmp = BUILD / f"{lib.stem}.{tag}.so"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", str(tmp), *map(str, objs)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     for o in objs:
         o.unlink(missing_ok=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

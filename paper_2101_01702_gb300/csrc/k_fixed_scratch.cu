@@ -125,5 +125,6 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     if (bits & LBMK_BIT_NEWTON) return LBM_ERR_NEWTON;
     if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
     if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
+    if (bits & LBMK_BIT_BOUNDS) return LBM_ERR_BOUNDS;
     return LBM_OK;
 }

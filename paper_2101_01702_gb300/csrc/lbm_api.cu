@@ -121,6 +121,7 @@ int map_status(unsigned bits)
     if (bits & LBMK_BIT_NEWTON) return LBM_ERR_NEWTON;
     if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
     if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
+    if (bits & LBMK_BIT_BOUNDS) return LBM_ERR_BOUNDS;
     return LBM_OK;
 }
 
@@ -675,6 +676,7 @@ const char *lbm_strerror(int s)
     case LBM_ERR_NONFINITE: return "non-finite density, energy or population";
     case LBM_ERR_NEGATIVE: return "negative species density";
     case LBM_ERR_PIVOT: return "non-finite pivot in the Stefan-Maxwell solve";
+    case LBM_ERR_BOUNDS: return "index out of bounds (checked build)";
     case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown status";
     }

@@ -17,6 +17,7 @@
 #define LBMK_BIT_NONFINITE 2u
 #define LBMK_BIT_NEGATIVE 4u
 #define LBMK_BIT_PIVOT 8u
+#define LBMK_BIT_BOUNDS 16u     // checked builds: an index derived from the geometry left its buffer
 
 // Per-node record in the macro buffer: macro_double_rows(M) rows of
 // doubles, then rec_rows(M).total rows of the storage type (float in mixed

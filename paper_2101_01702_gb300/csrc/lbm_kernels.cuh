@@ -39,6 +39,14 @@
 #ifndef LBMK_FAST
 #define LBMK_FAST 0
 #endif
+// LBMK_CHECKED 1: every index the kernels derive from the lattice geometry
+// (pulls from neighbours and ghost planes, stencil neighbours, ghost-node
+// sources, batch ranges) is checked against its buffer before use; a bad one
+// sets LBMK_BIT_BOUNDS in the status word and is replaced by 0, so that
+// nothing traps and no access leaves its buffer.  A testing build.
+#ifndef LBMK_CHECKED
+#define LBMK_CHECKED 0
+#endif
 
 #if LBMK_MIXED
 typedef float Real;
@@ -121,6 +129,19 @@ __device__ __forceinline__ void for_dirs(F &&f)
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 __device__ __forceinline__ void flag(unsigned *status, unsigned bit) { atomicOr(status, bit); }
+
+// Checked builds: records a failed index check; always true otherwise.
+__device__ __forceinline__ bool index_ok(bool ok, unsigned *status)
+{
+#if LBMK_CHECKED
+    if (!ok) flag(status, LBMK_BIT_BOUNDS);
+    return ok;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
 
 // ---------------------------------------------------------------------
 // Population storage (see pop_bytes_for).
@@ -222,8 +243,14 @@ __device__ __forceinline__ Src src_of(int i, const PullIdx &p, const StepArgs &a
     const int xs = p.xs[CX(i) + 1];
     const int gp = p.gp[CX(i) + 1];
     const int yz = p.yz[(CY(i) + 1) + 3 * (CZ(i) + 1)];
-    if (gp >= 0) return Src{true, gp, (size_t)yz};
-    return Src{false, 0, (size_t)xs + (size_t)a.nx * yz};
+    if (gp >= 0) {
+        const int nlat = a.nseg > 1 ? a.nseg : 1;
+        if (!index_ok(gp < 2 * nlat && yz >= 0 && yz < a.ny * a.nz, a.status)) return Src{false, 0, 0};
+        return Src{true, gp, (size_t)yz};
+    }
+    const size_t idx = (size_t)xs + (size_t)a.nx * yz;
+    if (!index_ok(xs >= 0 && xs < a.nx && yz >= 0 && idx < (size_t)a.N, a.status)) return Src{false, 0, 0};
+    return Src{false, 0, idx};
 }
 
 __device__ __forceinline__ double load_ghost(const StepArgs &a, int plane_idx, int s, int i, size_t yz)
@@ -305,9 +332,10 @@ __device__ __forceinline__ void make_stencil(StencilIdx &t, const Node &nd, cons
 }
 
 template <int I>
-__device__ __forceinline__ size_t nb_of(const StencilIdx &t)
+__device__ __forceinline__ size_t nb_of(const StencilIdx &t, const StepArgs &a)
 {
-    return (size_t)t.xs[CX(I) + 1] + t.row[(CY(I) + 1) + 3 * (CZ(I) + 1)];
+    const size_t nb = (size_t)t.xs[CX(I) + 1] + t.row[(CY(I) + 1) + 3 * (CZ(I) + 1)];
+    return index_ok(nb < (size_t)a.N, a.status) ? nb : 0;
 }
 
 __device__ __forceinline__ Real *rec(const StepArgs &a)
@@ -450,6 +478,11 @@ __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
         nd.x0 = e.x;
         nd.x1 = e.y;
         nd.k = e.z;
+        if (!index_ok(e.x <= nd.x && nd.x < e.y && e.y <= a.nx && e.z >= 0 && e.z < a.nseg, a.status)) {
+            nd.x0 = nd.x;
+            nd.x1 = nd.x + 1;
+            nd.k = 0;
+        }
     } else {
         nd.x0 = 0;
         nd.x1 = a.nx;
@@ -572,7 +605,8 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
         x0 = r.x;
         x1 = r.y;
     }
-    const size_t n = (size_t)(side ? x1 - 1 : x0) + (size_t)a.nx * yz;
+    size_t n = (size_t)(side ? x1 - 1 : x0) + (size_t)a.nx * yz;
+    if (!index_ok(x0 >= 0 && x0 < x1 && x1 <= a.nx && n < (size_t)a.N, a.status)) n = 0;
     const PopView v = view(a.src, a);
     double rho_a[M], rho = 0.0, j[3] = {0, 0, 0}, rhoE = 0.0;
     double rest = 0.0;
@@ -1117,7 +1151,7 @@ __global__ void __launch_bounds__(LBMK_MAXBLOCK) k_grad(StepArgs a)
     Real d[3] = {0, 0, 0};
     for_dirs<0, LBMK_Q>([&](auto dd) {
         constexpr int I = decltype(dd)::value;
-        const size_t nb = nb_of<I>(st);
+        const size_t nb = nb_of<I>(st, a);
         if (CX(I)) d[0] += (Real)(WI(I) * CX(I)) * Phi[nb];
         if (CY(I)) d[1] += (Real)(WI(I) * CY(I)) * Phi[N + nb];
         if (CZ(I)) d[2] += (Real)(WI(I) * CZ(I)) * Phi[2 * N + nb];
@@ -1163,7 +1197,7 @@ __global__ void __launch_bounds__(LBMK_MAXBLOCK) k_step_g(StepArgs a)
         for_dirs<0, LBMK_Q>([&](auto dd) {
             constexpr int I = decltype(dd)::value;
             if constexpr (I != REST) {
-                const size_t nb = nb_of<I>(st);
+                const size_t nb = nb_of<I>(st, a);
                 Real hy = 0;
 #pragma unroll
                 for (int s = 0; s < M; ++s) hy += Hl[s] * Yf[s * N + nb];
@@ -1256,7 +1290,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
         for_dirs<0, LBMK_Q>([&](auto dd) {
             constexpr int I = decltype(dd)::value;
             if constexpr (I != REST) {
-                const size_t nb = nb_of<I>(st);
+                const size_t nb = nb_of<I>(st, a);
                 constexpr Real wx = (Real)(WI(I) * CX(I)), wy = (Real)(WI(I) * CY(I)), wz = (Real)(WI(I) * CZ(I));
                 if (CX(I)) X[0] += wx * G[nb];
                 if (CY(I)) X[1] += wy * G[N + nb];

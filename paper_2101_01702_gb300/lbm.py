@@ -27,6 +27,7 @@ LBM_ERR_CUDA = -2
 LBM_ERR_NEWTON = -3
 LBM_ERR_NONFINITE = -4
 LBM_ERR_NEGATIVE = -5
+LBM_ERR_BOUNDS = -7
 LBM_ERR_PIVOT = -6
 LBM_ERR_UNSUPPORTED = -8
 LBM_BC_PERIODIC = 0
