@@ -220,7 +220,7 @@ def run_ours(args):
     # stream with CUDA events between the kernels (one wait at the end);
     # the events give the whole-run time and each kernel's launch times.
     s = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
-    blocks = s.autotune(trials=3)                         # launch shapes, outside the timed region
+    blocks = None if args.skip_autotune else s.autotune(trials=3)   # launch shapes, outside the timed region
     s.step(args.warmup)
     torch.cuda.synchronize()
     barrier()
@@ -408,7 +408,7 @@ def run_flames(args):
         return replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
 
     batch = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
-    blocks = batch.autotune(trials=3)                     # launch shapes, outside the timed region
+    blocks = None if args.skip_autotune else batch.autotune(trials=3)   # launch shapes, outside the timed region
     batch.step(args.warmup)
     with ClockSampler(local) as clk:
         ms_plain = timed(lambda: batch.step_async(K))
@@ -513,6 +513,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_fast", "fp64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-fast", action="store_true")
+    ap.add_argument("--skip-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])

@@ -73,11 +73,12 @@ typedef double WReal;
 // 256^3 nine-species lattice: the moment pass runs fastest at 5 blocks in
 // the fast mixed unit (96 registers, some spilled; latency bound) and at 3
 // in the double unit; with its double Stefan-Maxwell solve the mixed unit
-// is FP64-bound and insensitive to it (2..5 within 1 %).  The species and
-// mixture collision runs fastest at 3 blocks in the mixed units (168
-// registers) and unconstrained in the double unit.
+// is FP64-bound and nearly insensitive to it (1..5 within 1.4 %, 3 best,
+// with the fewest spills of the capped choices).  The species and mixture
+// collision runs fastest at 3 blocks in the mixed units (168 registers) and
+// unconstrained in the double unit.
 #ifndef LBMK_PRE_MINB
-#define LBMK_PRE_MINB (LBMK_MIXED ? 5 : 3)
+#define LBMK_PRE_MINB (LBMK_MIXED && LBMK_FAST ? 5 : 3)
 #endif
 #ifndef LBMK_STEP_MINB
 #define LBMK_STEP_MINB (LBMK_MIXED ? 3 : 1)
