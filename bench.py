@@ -40,14 +40,14 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions;
 #   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 FP64_FLOPS_PER_NODE = {
-    "mixed": {"k_pre": 2079.2, "k_chem": 1172.0, "k_step_g": 163.0, "k_step": 18.0},
-    "mixed_fast": {"k_pre": 723.0, "k_chem": 646.0, "k_step_g": 163.0, "k_step": 18.0},
+    "mixed": {"k_pre": 2054.4, "k_chem": 1172.0, "k_step_g": 165.0, "k_step": 18.0},
+    "mixed_fast": {"k_pre": 723.0, "k_chem": 646.0, "k_step_g": 165.0, "k_step": 18.0},
     "fp64": {"k_pre": 2859.4, "k_chem": 1172.0, "k_step_g": 737.0, "k_step": 12534.0},
 }
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2945.6, "k_chem": 64.6, "k_step_g": 600.4, "k_step": 2402.8},
-    "mixed_fast": {"k_pre": 2244.4, "k_chem": 64.5, "k_step_g": 600.1, "k_step": 2402.4},
-    "fp64": {"k_pre": 3410.1, "k_chem": 138.2, "k_step_g": 699.9, "k_step": 4464.3},
+    "mixed": {"k_pre": 2105.5, "k_chem": 64.9, "k_step_g": 600.3, "k_step": 2401.8},
+    "mixed_fast": {"k_pre": 2275.2, "k_chem": 64.5, "k_step_g": 600.5, "k_step": 2401.9},
+    "fp64": {"k_pre": 3415.9, "k_chem": 138.5, "k_step_g": 699.7, "k_step": 4463.9},
 }
 
 
