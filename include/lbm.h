@@ -23,6 +23,10 @@
  *     are never freed by the library.  Host arrays passed to lbm_create are
  *     copied; the library keeps no pointer to them.
  *   - All GPU work is ordered on the CUDA stream given to lbm_create.
+ *   - A context belongs to the CUDA device that is current when lbm_create
+ *     is called; every later call on it that touches the GPU must be made
+ *     with that device current, else it returns LBM_ERR_ARG.  Contexts on
+ *     different devices of one process share no state.
  */
 #ifndef LBM_H
 #define LBM_H

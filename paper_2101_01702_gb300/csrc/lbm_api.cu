@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
 #include <mutex>
 
 #include "../../include/lbm.h"
@@ -34,20 +36,23 @@ struct lbm_ctx {
     int graph_cur;           // value of cur the graph starts from
     bool refs_fixed;         // rest references set by lbm_set_references
     int bs[LBMK_NKERNELS];   // threads per block of each kernel (lbm_autotune)
+    int dev;                 // CUDA device current at lbm_create
 };
 
 namespace {
 
-// Constant-memory slots of each kernel unit (precision).  Contexts whose
-// packed tables are identical -- the same mechanism and, in the mixed
-// modes, the same rest references -- share a slot; a slot is uploaded when
-// it is taken and reused once no context refers to it.
+// Constant-memory slots of each kernel unit (precision) on each device.
+// Contexts on one device whose packed tables are identical -- the same
+// mechanism and, in the mixed modes, the same rest references -- share a
+// slot; a slot is uploaded when it is taken and reused once no context
+// refers to it.  Constant memory is per device, so each device keeps its
+// own table: a slot uploaded on one device holds nothing on another.
 struct SlotTable {
     int refs[LBMK_SLOTS];
     MechConst mc[LBMK_SLOTS];
 };
 std::mutex g_slot_mutex;
-SlotTable g_slots[3];
+std::map<int, std::array<SlotTable, 3>> g_slots;    // device -> precision -> slots
 
 bool supported_M(int M) { return M == 2 || M == 3 || M == 9; }
 
@@ -65,13 +70,14 @@ const lbmk::PrecisionOps kOps[3] = {
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
-// A slot of precision p holding mc (shared or newly uploaded on stream and
-// waited for); -1 when every slot holds other tables.
-int acquire_slot(int p, const MechConst &mc, cudaStream_t stream, int *err)
+// A slot of precision p on device dev (the current device) holding mc
+// (shared or newly uploaded on stream and waited for); -1 when every slot
+// holds other tables.
+int acquire_slot(int dev, int p, const MechConst &mc, cudaStream_t stream, int *err)
 {
     *err = LBM_OK;
     std::lock_guard<std::mutex> lk(g_slot_mutex);
-    SlotTable &t = g_slots[p];
+    SlotTable &t = g_slots[dev][p];
     for (int s = 0; s < LBMK_SLOTS; ++s)
         if (t.refs[s] > 0 && memcmp(&t.mc[s], &mc, sizeof(MechConst)) == 0) {
             ++t.refs[s];
@@ -91,22 +97,34 @@ int acquire_slot(int p, const MechConst &mc, cudaStream_t stream, int *err)
     return -1;
 }
 
-void release_slot(int p, int s)
+void release_slot(int dev, int p, int s)
 {
     if (s < 0 || s >= LBMK_SLOTS) return;
     std::lock_guard<std::mutex> lk(g_slot_mutex);
-    if (g_slots[p].refs[s] > 0) --g_slots[p].refs[s];
+    auto it = g_slots.find(dev);
+    if (it != g_slots.end() && it->second[p].refs[s] > 0) --it->second[p].refs[s];
+}
+
+// LBM_OK when the calling thread's current device is the one c was created
+// on; its buffers, stream and constant-memory slot live there.
+int on_ctx_device(const lbm_ctx *c)
+{
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) return LBM_ERR_CUDA;
+    return d == c->dev ? LBM_OK : LBM_ERR_ARG;
 }
 
 // Moves context c to a slot holding c->mc (after its stream has drained,
 // so that none of its kernels still reads the old slot).
 int reslot(lbm_ctx *c)
 {
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBM_ERR_CUDA;
     int err;
-    const int s = acquire_slot(c->lat.precision, c->mc, c->stream, &err);
+    const int s = acquire_slot(c->dev, c->lat.precision, c->mc, c->stream, &err);
     if (s < 0) return err;
-    release_slot(c->lat.precision, c->slot);
+    release_slot(c->dev, c->lat.precision, c->slot);
     c->slot = s;
     if (c->graph) {                      // captured with the old slot
         cudaGraphExecDestroy(c->graph);
@@ -250,15 +268,18 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     r = lbm_pack_tables(sp, mech, mc);
     if (r != LBM_OK) return r;
 
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
     int err = LBM_OK;
-    const int slot = acquire_slot(lat->precision, mc, (cudaStream_t)cuda_stream, &err);
+    const int slot = acquire_slot(dev, lat->precision, mc, (cudaStream_t)cuda_stream, &err);
     if (slot < 0) return err;
 
     lbm_ctx *c = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
     if (!c) {
-        release_slot(lat->precision, slot);
+        release_slot(dev, lat->precision, slot);
         return LBM_ERR_ARG;
     }
+    c->dev = dev;
     c->lat = *lat;
     c->M = M;
     c->S = M + 1;
@@ -306,6 +327,8 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
 int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, double P)
 {
     if (!c || !X || !T || !(P > 0)) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     const size_t N = (size_t)c->N, M = (size_t)c->M;
     const bool dX = is_device_ptr(X), dT = is_device_ptr(T), du = u ? is_device_ptr(u) : dX;
     if (dX != dT || dX != du) return LBM_ERR_ARG;     // all host or all device
@@ -359,6 +382,8 @@ int lbm_init(lbm_ctx *c, const double *X, const double *T, const double *u, doub
 int lbm_step_async(lbm_ctx *c, int n)
 {
     if (!c || n < 0) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     for (int t = 0; t < n; ++t) {
         StepArgs a = args_of(c);
         const int e = ops(c->lat.precision).step(a, nullptr);
@@ -371,6 +396,8 @@ int lbm_step_async(lbm_ctx *c, int n)
 int lbm_step_graph(lbm_ctx *c, int n)
 {
     if (!c || n < 0) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     if (c->stream == nullptr) return LBM_ERR_UNSUPPORTED;   // the legacy default stream cannot be captured
     if (!c->graph) {
         cudaGraph_t g = nullptr;
@@ -504,6 +531,8 @@ int lbm_set_blocks(lbm_ctx *c, const int *blocks)
 int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
 {
     if (!c || n < 0 || !phase_ms) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     for (int k = 0; k <= LBM_PHASES; ++k) phase_ms[k] = 0.0;
     if (n == 0) return lbm_sync(c);
     // LBM_PHASES + 1 events per step, all recorded before the one wait, so
@@ -545,6 +574,8 @@ int lbm_step_timed(lbm_ctx *c, int n, double *phase_ms)
 int lbm_sync(lbm_ctx *c)
 {
     if (!c) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     unsigned bits = 0;
     int st = check_cuda(cudaMemcpyAsync(&bits, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     if (st == LBM_OK) st = check_cuda(cudaStreamSynchronize(c->stream));
@@ -581,6 +612,8 @@ size_t lbm_moments_count(const lbm_ctx *c, unsigned mask)
 int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
 {
     if (!c || !out || mask == 0 || (mask & ~255u)) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     const size_t count = lbm_moments_count(c, mask);
     const bool dev = is_device_ptr(out);
     double *target = out;
@@ -601,6 +634,8 @@ int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
 int lbm_get_populations(lbm_ctx *c, double *host_out)
 {
     if (!c || !host_out) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
     const size_t cnt = (size_t)c->S * LBMK_Q * c->N;
     int st = check_cuda(cudaStreamSynchronize(c->stream));
     if (st != LBM_OK) return st;
@@ -661,7 +696,7 @@ int lbm_destroy(lbm_ctx *c)
     if (c->status) cudaFree(c->status);
     if (c->xseg) cudaFree(c->xseg);
     if (c->segs) cudaFree(c->segs);
-    release_slot(c->lat.precision, c->slot);
+    release_slot(c->dev, c->lat.precision, c->slot);
     free(c);
     return LBM_OK;
 }

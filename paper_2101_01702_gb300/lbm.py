@@ -224,11 +224,26 @@ def lbm_strerror(st: int) -> str:
 # ---------------------------------------------------------------------------
 # Convenience: a problem description plus torch-owned device buffers
 # ---------------------------------------------------------------------------
+def _on_device(method):
+    """Runs a Solver method with the solver's device current: the library
+    binds a context to the device current at lbm_create and rejects calls
+    made from another."""
+
+    def wrapped(self, *args, **kw):
+        with self.torch.cuda.device(self.device):
+            return method(self, *args, **kw)
+
+    wrapped.__name__ = method.__name__
+    wrapped.__doc__ = method.__doc__
+    return wrapped
+
+
 class Solver:
     """Owns torch buffers for one lattice and drives the C ABI.
 
     lattice/species/mech follow workload.problem (numpy arrays).  The
-    tables are passed to lbm_create, which copies them.
+    tables are passed to lbm_create, which copies them.  Every call runs
+    with the solver's device current, whichever device the caller has.
     """
 
     def __init__(self, lattice, species, mech, precision: int = LBM_FP64, device="cuda", stream=None):
@@ -236,6 +251,8 @@ class Solver:
 
         self.torch = torch
         self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.M = species.M
         self.S = self.M + 1
@@ -275,7 +292,8 @@ class Solver:
             self.ghost = torch.empty(max(gh_b, 16), dtype=torch.uint8, device=self.device)
         self.bufs = lbm_buffers(self.pop[0].data_ptr(), self.pop[1].data_ptr(), self.macro.data_ptr(),
                                 self.ghost.data_ptr() if gh_b else None, pop_b, mac_b, gh_b)
-        self.ctx = lbm_create(self.lat, self.sp, self.mech, self.bufs, self.stream.cuda_stream)
+        with torch.cuda.device(self.device):
+            self.ctx = lbm_create(self.lat, self.sp, self.mech, self.bufs, self.stream.cuda_stream)
 
     @classmethod
     def from_problem(cls, prob, precision: int = LBM_FP64, init: bool = True, **kw):
@@ -284,6 +302,7 @@ class Solver:
             s.init(prob.init.X, prob.init.T, prob.init.u, prob.init.P)
         return s
 
+    @_on_device
     def close(self):
         if getattr(self, "ctx", None):
             lbm_destroy(self.ctx)
@@ -295,6 +314,7 @@ class Solver:
         except Exception:
             pass
 
+    @_on_device
     def init(self, X, T, u, P):
         """X[M,N], T[N], u[3,N] or None: numpy (host) or torch (device) arrays."""
         torch = self.torch
@@ -312,15 +332,18 @@ class Solver:
             st = lbm_init(self.ctx, Xh.ctypes.data, Th.ctypes.data, uh.ctypes.data if uh is not None else None, P)
         _check(st, "lbm_init")
 
+    @_on_device
     def step(self, n: int = 1, check: bool = True) -> int:
         st = lbm_step(self.ctx, n)
         if check:
             _check(st, "lbm_step")
         return st
 
+    @_on_device
     def step_async(self, n: int = 1):
         _check(lbm_step_async(self.ctx, n), "lbm_step_async")
 
+    @_on_device
     def autotune(self, trials: int = 3) -> dict:
         """Picks each kernel's block size by timing it on the current state
         (results unchanged); returns the choice per kernel."""
@@ -329,6 +352,7 @@ class Solver:
         return dict(zip(("ghost", "moments", "rates", "gradients", "energy_collision", "species_collision"),
                         bs.tolist()))
 
+    @_on_device
     def set_blocks(self, blocks):
         """Block sizes of the six kernels in launch order (see autotune)."""
         _check(lbm_set_blocks(self.ctx, blocks), "lbm_set_blocks")
@@ -339,13 +363,16 @@ class Solver:
         _check(lbm_get_references(self.ctx, ref), "lbm_get_references")
         return ref
 
+    @_on_device
     def set_references(self, ref):
         _check(lbm_set_references(self.ctx, ref), "lbm_set_references")
 
+    @_on_device
     def step_graph(self, n: int = 1):
         """n steps through the captured two-step CUDA graph (no wait)."""
         _check(lbm_step_graph(self.ctx, n), "lbm_step_graph")
 
+    @_on_device
     def step_timed(self, n: int = 1):
         """Runs n steps; returns per-phase device milliseconds summed over
         them (ghost, moments, production rates, gradients, energy collision,
@@ -355,9 +382,11 @@ class Solver:
         _check(lbm_step_timed(self.ctx, n, ph), "lbm_step_timed")
         return ph
 
+    @_on_device
     def sync(self) -> int:
         return lbm_sync(self.ctx)
 
+    @_on_device
     def moments(self, mask: int = LBM_F_RHO_A | LBM_F_RHOU | LBM_F_RHOE | LBM_F_T, device: bool = False):
         """Dictionary of fields (numpy on host, or torch on the device)."""
         torch = self.torch
@@ -380,6 +409,7 @@ class Solver:
             res["j_a"] = res["j_a"].reshape(M, 3, N)
         return res
 
+    @_on_device
     def populations(self) -> np.ndarray:
         out = np.empty((self.S, 27, self.N), dtype=np.float64)
         _check(lbm_get_populations(self.ctx, out), "lbm_get_populations")
