@@ -33,6 +33,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "lbm_internal.h"
 
@@ -1491,14 +1492,15 @@ int launch_one(const StepArgs &a, int k)
         // blocks needing more than 48 KB of dynamic shared memory opt in,
         // once per device (only tuned block sizes do; the default never)
         if (chem_smem<M>(bs) > 48 * 1024) {
-            static unsigned long long opted = 0;     // bit d: device d has opted in
+            static std::atomic<unsigned long long> opted{0};   // bit d: device d has opted in
             int dev = 0;
             if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
-            if (!(opted >> dev & 1ull)) {
+            if (!(opted.load() >> dev & 1ull)) {
+                // idempotent, so two threads racing here both succeed
                 const cudaError_t e = cudaFuncSetAttribute(k_chem<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                            (int)chem_smem<M>(LBMK_MAXBLOCK));
                 if (e != cudaSuccess) return (int)e;
-                opted |= 1ull << dev;
+                opted.fetch_or(1ull << dev);
             }
         }
         k_chem<M><<<grid_for(a.N, bs), bs, chem_smem<M>(bs), a.stream>>>(a);
