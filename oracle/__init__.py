@@ -66,6 +66,8 @@ def lib():
         L.orc_thermo.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp, _dp]
         L.orc_temperature.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
         L.orc_rates.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
+        L.orc_heat_release.restype = C.c_double
+        L.orc_heat_release.argtypes = [C.c_void_p, _dp, C.c_double]
         L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
         L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
         L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
@@ -184,6 +186,11 @@ class Oracle:
         w = np.empty(self.M)
         lib().orc_rates(self._h, _d(rho_a), float(T), _d(w))
         return w
+
+    def heat_release(self, rho_a, T):
+        """hdot^c = -sum_a H_a rho_dot_a at one node state (Sec. 5b)."""
+        rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
+        return float(lib().orc_heat_release(self._h, _d(rho_a), float(T)))
 
     def diffusion_velocities(self, Y, ua_minus_u, T):
         Y = np.ascontiguousarray(Y, dtype=np.float64)

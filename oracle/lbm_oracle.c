@@ -31,6 +31,7 @@
  *   q^*, q^diff, q^corr .............................. Eqs. (gstareq1mom), (qdiff), (corrFourier)
  *   omega from viscosity, omega_1 from conductivity . Eqs. (mu), (lambda)
  *   slaving of the last species ...................... Eq. (strongest)
+ *   heat release rate hdot^c ......................... Sec. 5b (circular flame)
  *
  * Readings where the paper is silent (all recorded in the design notes):
  *   - lattice gradients: d_alpha phi(x) = (1/theta) sum_i w_i c_ia phi(x+c_i),
@@ -851,6 +852,18 @@ int orc_temperature(const orc_state *s, const double *Y, double e, double T_gues
 void orc_rates(const orc_state *s, const double *rho_a, double T, double *wdot)
 {
     production_rates(s, rho_a, T, wdot);
+}
+
+/* Heat release rate at a node state, Sec. 5b: hdot^c = -sum_a H_a rho_dot_a,
+ * with H_a the specific enthalpy (Eq. (specHa)) and rho_dot_a the
+ * production rates above. */
+double orc_heat_release(const orc_state *s, const double *rho_a, double T)
+{
+    double wdot[ORC_MAXM];
+    production_rates(s, rho_a, T, wdot);
+    double h = 0.0;
+    for (int a = 0; a < s->M; ++a) h -= H_spec(s, a, T) * wdot[a];
+    return h;
 }
 
 /* Diffusion velocities du[M][3] from Eq. (transform1) at a node state. */

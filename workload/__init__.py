@@ -18,4 +18,5 @@ from .configs import (  # noqa: F401
     flame_of_batch,
     mech9,
     mech3,
+    node_states,
 )

@@ -390,3 +390,29 @@ def flame_of_batch(prob: Problem, k: int) -> Problem:
     return Problem(f"{prob.name}_flame{k}", LatticeSpec(Lk, lat.ny, lat.nz, lat.bc_x), prob.species, prob.mech,
                    InitFields(X=X, T=T, u=None, P=prob.init.P), steps=prob.steps)
 
+
+
+def node_states(M: int, n: int, seed: int = 2101, T_range=(700.0, 2600.0), rho_range=(0.2, 1.2),
+                absent_frac: float = 0.1):
+    """n seeded node states (rho_a [M, n], T [n]) for checks of the node
+    functions (production rates, heat release and its derivatives).
+
+    Draw order (numpy PCG64, one generator): T [n] uniform in T_range; total
+    density [n] uniform in rho_range; log10 weights [n, M] uniform in
+    [-6, 0]; absence flags [n, M] (uniform < absent_frac).  A species flagged
+    absent gets weight 0, except the largest-weight species of each state;
+    the weights are normalised per state to mass fractions and scaled by the
+    total density.  Trace species span six decades and about one species in
+    ten is exactly absent, so that products of concentrations with a zero
+    factor occur.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    T = rng.uniform(T_range[0], T_range[1], size=n)
+    rho = rng.uniform(rho_range[0], rho_range[1], size=n)
+    wts = 10.0 ** rng.uniform(-6.0, 0.0, size=(n, M))
+    absent = rng.uniform(size=(n, M)) < absent_frac
+    absent[np.arange(n), np.argmax(wts, axis=1)] = False
+    wts[absent] = 0.0
+    Y = wts / wts.sum(axis=1, keepdims=True)
+    rho_a = np.ascontiguousarray((Y * rho[:, None]).T)
+    return rho_a, np.ascontiguousarray(T)
