@@ -246,13 +246,60 @@ int lbm_sync(lbm_ctx *ctx);
  *   LBM_F_J_A    species momenta rho_a u_a, 3M rows (a-major)
  *   LBM_F_RHO_DOT  mass production rates rho_dot_a of the mechanism at
  *                (rho_a, T), M rows (Eq. (sumRhoDot); per lattice time unit)
+ *   LBM_F_HRR    heat release rate hdot^c = -sum_a H_a rho_dot_a, 1 row
+ *                (Sec. 5b; H_a the specific enthalpy of Eq. (specHa))
  * Waits for the stream before returning. */
 enum { LBM_F_RHO_A = 1, LBM_F_RHOU = 2, LBM_F_RHOE = 4, LBM_F_T = 8, LBM_F_P = 16,
-       LBM_F_Y = 32, LBM_F_J_A = 64, LBM_F_RHO_DOT = 128 };
+       LBM_F_Y = 32, LBM_F_J_A = 64, LBM_F_RHO_DOT = 128, LBM_F_HRR = 256 };
 int lbm_moments(lbm_ctx *ctx, unsigned mask, double *out);
 
 /* Number of doubles lbm_moments writes for mask. */
 size_t lbm_moments_count(const lbm_ctx *ctx, unsigned mask);
+
+/* Heat-release objective and its sensitivities at the current time level
+ * (the state lbm_moments reports).  The heat release rate of Sec. 5b,
+ * hdot^c = -sum_a H_a rho_dot_a, is written per reaction as
+ * -sum_k dH_k q_k with dH_k = sum_a W_a (nu''_ak - nu'_ak) H_a(T) and the
+ * rate of progress q_k of the mechanism (Eqs. (sumRhoDot), (specHa)).
+ *   J         host, double: the sum of hdot^c over the nodes (required)
+ *   dJ_dlogA  host, double [R], or NULL: dJ/d ln A_k, A_k the
+ *             pre-exponential factor of reaction k (that of the
+ *             high-pressure rate for a falloff reaction), all else fixed
+ *   dJ_dT     host or device, double [N], or NULL: d hdot^c/dT at each node
+ *             with its densities fixed
+ *   dJ_drho   host or device, double [M][N], or NULL: d hdot^c/d rho_a at
+ *             each node with T and the other densities fixed (all M
+ *             densities independent, the slaved one included)
+ * J and dJ_dlogA are summed on the GPU in a fixed order, so that they
+ * repeat from run to run.  These are the chemistry terms of an adjoint of
+ * the step (the paper has none; the transposed step is not part of this
+ * library).  The second population buffer serves as scratch, as in
+ * lbm_moments.  Waits for the stream; returns like lbm_sync, or
+ * LBM_ERR_ARG for a NULL ctx or J. */
+int lbm_heat_release(lbm_ctx *ctx, double *J, double *dJ_dlogA, double *dJ_dT, double *dJ_drho);
+
+/* The step's chemistry at n given node states, for checks of the node
+ * functions on inputs of the caller's choice.  Inputs, device:
+ *   rho_a [M][n] species densities, T [n] temperatures.
+ * Outputs, device, each NULL to skip:
+ *   rho_dot     [M][n]  mass production rates, evaluated as the step does
+ *                       (Eq. (sumRhoDot); in the precision unit's arithmetic)
+ *   hdot        [n]     heat release rate -sum_a H_a rho_dot_a (Sec. 5b)
+ *   dhdot_dT    [n]     its derivative in T at fixed densities
+ *   dhdot_drho  [M][n]  its derivatives in rho_a at fixed T
+ *   dhdot_dlogA [R][n]  its derivatives in ln A_k (as in lbm_heat_release)
+ * Waits for the stream; LBM_ERR_ARG for n < 0, a NULL input or a host
+ * pointer; else returns like lbm_sync. */
+int lbm_chemistry_at(lbm_ctx *ctx, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                     double *dhdot_dT, double *dhdot_drho, double *dhdot_dlogA);
+
+/* The step's Newton temperature (Eq. (temperature)) at n given node states:
+ * mass fractions Y [M][n], specific internal energy e [n] (including the
+ * energies of formation; e = rho E / rho - u^2/2) and starting points
+ * T_guess [n]; temperatures to T [n].  All device.  Waits for the stream;
+ * LBM_ERR_ARG for n < 0, NULL or host pointers; LBM_ERR_NEWTON when an
+ * iteration did not converge. */
+int lbm_temperature_at(lbm_ctx *ctx, int n, const double *Y, const double *e, const double *T_guess, double *T);
 
 /* Current post-collision populations as absolute doubles, layout
  * [M+1][27][N], copied to host memory out.  Diagnostic accessor. */

@@ -46,4 +46,26 @@ int moments_mixed_fast(const StepArgs &a, unsigned mask, double *out)
 #undef CALL
 }
 
+int hrr_mixed_fast(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out)
+{
+#define CALL(M_) run_hrr<M_>(a, R, dT, drho, partial, out)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
+int chem_at_mixed_fast(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                      double *dT, double *drho, double *dA)
+{
+#define CALL(M_) run_chem_at<M_>(a, n, rho_a, T, rho_dot, hdot, dT, drho, dA)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
+int temperature_at_mixed_fast(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T)
+{
+#define CALL(M_) run_temperature_at<M_>(a, n, Y, e, T0, T)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 }  // namespace lbmk

@@ -62,11 +62,14 @@ size_t store_size(int precision) { return is_mixed(precision) ? sizeof(float) : 
 
 const lbmk::PrecisionOps kOps[3] = {
     {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64,
-     lbmk::launch_one_fp64},
+     lbmk::launch_one_fp64, lbmk::hrr_fp64,
+     lbmk::chem_at_fp64, lbmk::temperature_at_fp64},
     {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed,
-     lbmk::launch_one_mixed},
+     lbmk::launch_one_mixed, lbmk::hrr_mixed,
+     lbmk::chem_at_mixed, lbmk::temperature_at_mixed},
     {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
-     lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast},
+     lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast, lbmk::hrr_mixed_fast,
+     lbmk::chem_at_mixed_fast, lbmk::temperature_at_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -606,12 +609,13 @@ size_t lbm_moments_count(const lbm_ctx *c, unsigned mask)
     if (mask & LBM_F_Y) rows += c->M;
     if (mask & LBM_F_J_A) rows += 3 * (size_t)c->M;
     if (mask & LBM_F_RHO_DOT) rows += c->M;
+    if (mask & LBM_F_HRR) rows += 1;
     return rows * (size_t)c->N;
 }
 
 int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
 {
-    if (!c || !out || mask == 0 || (mask & ~255u)) return LBM_ERR_ARG;
+    if (!c || !out || mask == 0 || (mask & ~511u)) return LBM_ERR_ARG;
     const int od = on_ctx_device(c);
     if (od != LBM_OK) return od;
     const size_t count = lbm_moments_count(c, mask);
@@ -628,6 +632,68 @@ int lbm_moments(lbm_ctx *c, unsigned mask, double *out)
         int st = check_cuda(cudaMemcpyAsync(out, target, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         if (st != LBM_OK) return st;
     }
+    return lbm_sync(c);
+}
+
+int lbm_heat_release(lbm_ctx *c, double *J, double *dJ_dlogA, double *dJ_dT, double *dJ_drho)
+{
+    if (!c || !J) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    const size_t N = (size_t)c->N, M = (size_t)c->M;
+    const int R = c->mc.R;
+    const bool dT_dev = dJ_dT && is_device_ptr(dJ_dT), dr_dev = dJ_drho && is_device_ptr(dJ_drho);
+    // Scratch in the free population buffer: the rows bound for host
+    // memory, then the per-block partial sums and the totals.
+    double *stage = (double *)c->buf[1 - c->cur];
+    size_t off = 0;
+    double *dT = dJ_dT, *dr = dJ_drho;
+    if (dJ_dT && !dT_dev) { dT = stage + off; off += N; }
+    if (dJ_drho && !dr_dev) { dr = stage + off; off += M * N; }
+    off = (off + 31) & ~(size_t)31;
+    double *partial = stage + off;
+    off += (size_t)LBMK_HRR_BLOCKS * (1 + R);
+    double *tot = stage + off;
+    off += 1 + R;
+    if (off * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+    if (ops(c->lat.precision).hrr(args_of(c), R, dT, dr, partial, tot)) return LBM_ERR_CUDA;
+    double htot[1 + LBMK_MAXR];
+    int st = check_cuda(cudaMemcpyAsync(htot, tot, (1 + R) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (st == LBM_OK && dJ_dT && !dT_dev)
+        st = check_cuda(cudaMemcpyAsync(dJ_dT, dT, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (st == LBM_OK && dJ_drho && !dr_dev)
+        st = check_cuda(cudaMemcpyAsync(dJ_drho, dr, M * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (st == LBM_OK) st = lbm_sync(c);
+    if (st != LBM_OK) return st;
+    *J = htot[0];
+    if (dJ_dlogA)
+        for (int k = 0; k < R; ++k) dJ_dlogA[k] = htot[1 + k];
+    return LBM_OK;
+}
+
+int lbm_chemistry_at(lbm_ctx *c, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                     double *dhdot_dT, double *dhdot_drho, double *dhdot_dlogA)
+{
+    if (!c || n < 0 || (n > 0 && (!rho_a || !T))) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    if (n == 0) return LBM_OK;
+    const double *ptrs[7] = {rho_a, T, rho_dot, hdot, dhdot_dT, dhdot_drho, dhdot_dlogA};
+    for (const double *q : ptrs)
+        if (q && !is_device_ptr(q)) return LBM_ERR_ARG;
+    if (ops(c->lat.precision).chem_at(args_of(c), n, rho_a, T, rho_dot, hdot, dhdot_dT, dhdot_drho, dhdot_dlogA))
+        return LBM_ERR_CUDA;
+    return lbm_sync(c);
+}
+
+int lbm_temperature_at(lbm_ctx *c, int n, const double *Y, const double *e, const double *T_guess, double *T)
+{
+    if (!c || n < 0 || (n > 0 && (!Y || !e || !T_guess || !T))) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    if (n == 0) return LBM_OK;
+    if (!is_device_ptr(Y) || !is_device_ptr(e) || !is_device_ptr(T_guess) || !is_device_ptr(T)) return LBM_ERR_ARG;
+    if (ops(c->lat.precision).temperature_at(args_of(c), n, Y, e, T_guess, T)) return LBM_ERR_CUDA;
     return lbm_sync(c);
 }
 

@@ -162,6 +162,27 @@ int ref_stats_fp64(const StepArgs &a, const double *X, const double *T, double P
 int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 
+// heat release rate and its sensitivities of the state in src (lbm_heat_release):
+// dT [N] and drho [M][N] (device, or null), partial LBMK_HRR_BLOCKS (1 + R)
+// doubles of scratch, out {sum hdot^c, sum d hdot^c/d ln A_k (R)}
+#define LBMK_HRR_BLOCKS 1024
+int hrr_fp64(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
+int hrr_mixed(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
+int hrr_mixed_fast(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
+
+// the step's chemistry and Newton temperature at n given node states
+// (lbm_chemistry_at, lbm_temperature_at; device arrays, outputs may be null)
+int chem_at_fp64(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                 double *dT, double *drho, double *dA);
+int chem_at_mixed(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                  double *dT, double *drho, double *dA);
+int chem_at_mixed_fast(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot,
+                       double *hdot, double *dT, double *drho, double *dA);
+int temperature_at_fp64(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T);
+int temperature_at_mixed(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T);
+int temperature_at_mixed_fast(const StepArgs &a, int n, const double *Y, const double *e, const double *T0,
+                              double *T);
+
 // one kernel of the step (LBMK_K_*) with the block size a.bs[kernel]
 int launch_one_fp64(const StepArgs &a, int kernel);
 int launch_one_mixed(const StepArgs &a, int kernel);
@@ -175,5 +196,9 @@ struct PrecisionOps {
     int (*moments)(const StepArgs &a, unsigned mask, double *out);
     int (*ref_stats)(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
     int (*launch_one)(const StepArgs &a, int kernel);
+    int (*hrr)(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
+    int (*chem_at)(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                   double *dT, double *drho, double *dA);
+    int (*temperature_at)(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T);
 };
 }  // namespace lbmk

@@ -467,10 +467,9 @@ __device__ void equilibria(const MechConst &mc, const double *rho_a, const doubl
     for (int i = 0; i < LBMK_Q; ++i) put(M, i, grad_dir(i, rhoE, q, Rt, tr3));
 }
 
-__device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
+// Coordinates and lattice range of node nd.n (0 <= nd.n < a.N).
+__device__ __forceinline__ void node_at(Node &nd, const StepArgs &a)
 {
-    nd.n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (nd.n >= a.N) return false;
     nd.x = nd.n % a.nx;
     const int r = nd.n / a.nx;
     nd.y = r % a.ny;
@@ -490,6 +489,13 @@ __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
         nd.x1 = a.nx;
         nd.k = 0;
     }
+}
+
+__device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
+{
+    nd.n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nd.n >= a.N) return false;
+    node_at(nd, a);
     return true;
 }
 
@@ -869,12 +875,21 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mas
         for (int d = 0; d < 3; ++d) out[(row + 3 * (M - 1) + d) * N + n] = jM[d];
         row += 3 * M;
     }
-    if (mask & 128u) {
+    if (mask & (128u | 256u)) {
         double conc[M];
 #pragma unroll
         for (int s = 0; s < M; ++s) conc[s] = rho_a[s] * mc.invW[s];
         molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, threadIdx.x, LBMK_BLOCK);
-        for (int s = 0; s < M; ++s) out[(row + s) * N + n] = mc.W[s] * (double)sh_w[s * LBMK_BLOCK + threadIdx.x];
+        if (mask & 128u) {
+            for (int s = 0; s < M; ++s) out[(row + s) * N + n] = mc.W[s] * (double)sh_w[s * LBMK_BLOCK + threadIdx.x];
+            row += M;
+        }
+        if (mask & 256u) {      // heat release rate, -sum_a H_a rho_dot_a
+            double h = 0.0;
+            for (int s = 0; s < M; ++s)
+                h = fma(-H_spec(mc, s, T), mc.W[s] * (double)sh_w[s * LBMK_BLOCK + threadIdx.x], h);
+            out[row * N + n] = h;
+        }
     }
 }
 
@@ -1654,6 +1669,295 @@ int run_ref_stats(const StepArgs &a, const double *X, const double *T, double P,
                                                                   LBMK_STAT_THREADS);
     k_stat_partial<M><<<nb, LBMK_STAT_THREADS, 0, a.stream>>>(a, X, T, P, scratch);
     k_stat_final<M><<<1, LBMK_STAT_THREADS, 0, a.stream>>>(scratch, nb, out);
+    return (int)cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------
+// Heat release rate hdot^c = -sum_a H_a rho_dot_a (Sec. 5b) of the state in
+// src (the state lbm_moments reports) and its partial derivatives there.
+// With the reaction enthalpy dH_k = sum_a W_a (nu''_ak - nu'_ak) H_a(T),
+// hdot^c = -sum_k dH_k q_k, and q_k = F_k (k_f P_f - k_r P_r) with
+//   k_f = A_k (T/T_ref)^b_k exp(-theta_k/T),  P_f, P_r the products of the
+//   reactant and product concentrations c_a = rho_a / W_a,
+//   k_r = k_f / K_c, ln K_c = -sum_a dnu_a g_a/(R_U T) + dn ln(P0/(r T)),
+//   F = 1, [M] = sum_a eff_a c_a (third body) or Pr/(1+Pr) with
+//   Pr = (k0/k_inf) [M] (Lindemann falloff; A_k is that of k_inf).
+// The derivatives are taken at fixed densities (for d/dT) and at fixed
+// temperature (for d/drho_a, every one of the M densities independent):
+//   d ln k_f/dT = (b + theta/T)/T,
+//   d ln K_c/dT = dH_k/(r T^2) - dn/T          (van 't Hoff; d(g_a/RT)/dT = -h_a/(R T^2)),
+//   d ln q_k/d ln A_k = 1, or Pr/(1+Pr) for falloff (Pr scales as 1/k_inf),
+//   d dH_k/dT = sum_a W_a dnu_a C_p,a.
+// Each block sums hdot^c and d hdot^c/d ln A_k over its nodes (grid-stride,
+// then a tree in shared memory, in a fixed order); k_hrr_final sums the
+// blocks in a fixed order, so that the totals repeat from run to run.
+// ---------------------------------------------------------------------
+constexpr int LBMK_HRR_THREADS = 128;
+
+// Specific heat C_p,a(T) = dH_a/dT.
+__device__ __forceinline__ double cp_spec(const MechConst &mc, int a, double T)
+{
+    const double *h = mc.hco[a];
+    return fma(fma(fma(fma(5.0 * h[4], T, 4.0 * h[3]), T, 3.0 * h[2]), T, 2.0 * h[1]), T, h[0]);
+}
+
+// hdot^c at one node state (T, rho_a) and its derivatives: d/dT into *dT,
+// d/drho_a into drho[M], and d/d ln A_k added to dA[k * stride] (k < R).
+template <int M>
+__device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const double *rho_a, double *dT_out,
+                                           double *drho, double *dA, int stride)
+{
+    const double invT = 1.0 / T, lnTr = log(T) - mc.log_T_ref;
+    const double lnc0 = log(mc.P0_over_r * invT);              // ln(P0/(r T))
+    double conc[M], WH[M], Wcp[M], g[M], dc[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        conc[s] = rho_a[s] * mc.invW[s];
+        WH[s] = mc.W[s] * H_spec(mc, s, T);
+        Wcp[s] = mc.W[s] * cp_spec(mc, s, T);
+        const double *gc = mc.gco[s];
+        g[s] = fma(gc[0], 1.0 - log(T),
+                   fma(fma(fma(fma(gc[4], T, gc[3]), T, gc[2]), T, gc[1]), T, fma(gc[5], invT, gc[6])));
+        dc[s] = 0.0;
+    }
+    double hdot = 0.0, dT = 0.0;
+    for (int k = 0; k < mc.R; ++k) {
+        const int nr = mc.nreac[k], np = mc.nprod[k];
+        double dH = 0.0, dHdT = 0.0, dG = 0.0, Pf = 1.0, Pp = 1.0;
+        for (int j = 0; j < nr; ++j) {
+            const int s = mc.reac[k][j];
+            dH -= WH[s];
+            dHdT -= Wcp[s];
+            dG -= g[s];
+            Pf *= conc[s];
+        }
+        for (int j = 0; j < np; ++j) {
+            const int s = mc.prod[k][j];
+            dH += WH[s];
+            dHdT += Wcp[s];
+            dG += g[s];
+            Pp *= conc[s];
+        }
+        const double lnkf = fma(mc.b[k], lnTr, fma(-mc.theta[k], invT, mc.log_A[k]));
+        const double kf = exp_table(lnkf);
+        const double dlnkf = fma(mc.theta[k], invT, mc.b[k]) * invT;
+        double kr = 0.0, dlnkr = 0.0;
+        if (mc.rev[k]) {
+            kr = exp_table(lnkf - fma((double)mc.dn[k], lnc0, -dG));       // k_f / K_c
+            dlnkr = dlnkf - (dH * invT * invT / mc.r_lat - mc.dn[k] * invT);
+        }
+        const double qf = kf * Pf, qr = kr * Pp, q0 = qf - qr;
+        double F = 1.0, dFdT = 0.0, dFdcM = 0.0, sA = 1.0;
+        const int type = mc.rtype[k];
+        if (type != 0) {
+            double cM = 0.0;
+#pragma unroll
+            for (int s = 0; s < M; ++s) cM = fma(mc.eff[k][s], conc[s], cM);
+            if (type == 1) {
+                F = cM;
+                dFdcM = 1.0;
+            } else {
+                const double k0r = exp_table(fma(mc.dlow[k][1], lnTr, fma(-mc.dlow[k][2], invT, mc.dlow[k][0])));
+                const double Pr = k0r * cM, i1 = 1.0 / (1.0 + Pr);
+                F = Pr * i1;
+                dFdcM = k0r * i1 * i1;
+                dFdT = F * i1 * fma(mc.dlow[k][2], invT, mc.dlow[k][1]) * invT;
+                sA = F;                                     // Pr/(1+Pr)
+            }
+        }
+        const double q = F * q0;
+        hdot -= dH * q;
+        dA[k * stride] -= dH * q * sA;
+        dT -= fma(dHdT, q, dH * fma(F, qf * dlnkf - qr * dlnkr, q0 * dFdT));
+        // d q/d c_b: the reactant and product products with one factor left out
+        const double wf = -dH * F * kf, wr = dH * F * kr;
+        for (int j = 0; j < nr; ++j) {
+            double pj = wf;
+            for (int i = 0; i < nr; ++i)
+                if (i != j) pj *= conc[mc.reac[k][i]];
+            dc[mc.reac[k][j]] += pj;
+        }
+        if (mc.rev[k])
+            for (int j = 0; j < np; ++j) {
+                double pj = wr;
+                for (int i = 0; i < np; ++i)
+                    if (i != j) pj *= conc[mc.prod[k][i]];
+                dc[mc.prod[k][j]] += pj;
+            }
+        if (type != 0) {
+            const double wm = -dH * q0 * dFdcM;
+#pragma unroll
+            for (int s = 0; s < M; ++s) dc[s] = fma(wm, mc.eff[k][s], dc[s]);
+        }
+    }
+    *dT_out = dT;
+#pragma unroll
+    for (int s = 0; s < M; ++s) drho[s] = dc[s] * mc.invW[s];      // c_a = rho_a / W_a
+    return hdot;
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_HRR_THREADS) k_hrr(StepArgs a, double *dT_out, double *drho_out,
+                                                          double *partial)
+{
+    __shared__ double sh_dA[LBMK_MAXR * LBMK_HRR_THREADS];
+    __shared__ double sh_J[LBMK_HRR_THREADS];
+    const MechConst &mc = c_mech[a.slot];
+    const int t = threadIdx.x, R = mc.R;
+    const size_t N = a.N;
+    for (int k = 0; k < R; ++k) sh_dA[k * LBMK_HRR_THREADS + t] = 0.0;
+    double Jt = 0.0;
+    for (int n = blockIdx.x * LBMK_HRR_THREADS + t; n < a.N; n += gridDim.x * LBMK_HRR_THREADS) {
+        Node nd;
+        nd.n = n;
+        node_at(nd, a);
+        PullIdx p;
+        make_pull(p, nd, a);
+        double rho_a[M];
+        Real ja[M][3];
+        Sums sm;
+        pull_moments<M, false>(mc, a, p, n, rho_a, ja, sm);
+        // the node state as in k_moments
+        const double rho = sm.rho;
+        double rest = 0.0;
+#pragma unroll
+        for (int s = 0; s < M - 1; ++s) rest += rho_a[s];
+        rho_a[M - 1] = rho - rest;
+        double Y[M];
+#pragma unroll
+        for (int s = 0; s < M; ++s) Y[s] = rho_a[s] / rho;
+        const double u[3] = {sm.j[0] / rho, sm.j[1] / rho, sm.j[2] / rho};
+        const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double eu[6];
+        mixture_energy_poly<M>(mc, Y, eu);
+        const double T = solve_T(eu, sm.rhoE / rho - 0.5 * usq, a.macro[DR_T * N + n], a.status);
+        double dT, drho[M];
+        Jt += hrr_node<M>(mc, T, rho_a, &dT, drho, sh_dA + t, LBMK_HRR_THREADS);
+        if (dT_out) dT_out[n] = dT;
+        if (drho_out)
+#pragma unroll
+            for (int s = 0; s < M; ++s) drho_out[(size_t)s * N + n] = drho[s];
+    }
+    sh_J[t] = Jt;
+    __syncthreads();
+    for (int w = LBMK_HRR_THREADS / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            sh_J[t] += sh_J[t + w];
+            for (int k = 0; k < R; ++k) sh_dA[k * LBMK_HRR_THREADS + t] += sh_dA[k * LBMK_HRR_THREADS + t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        double *o = partial + (size_t)blockIdx.x * (1 + R);
+        o[0] = sh_J[0];
+        for (int k = 0; k < R; ++k) o[1 + k] = sh_dA[k * LBMK_HRR_THREADS];
+    }
+}
+
+// The chemistry of n given node states (rho_a [M][n], T [n]; device): the
+// step's production rates (molar_production, as k_chem evaluates them) and
+// hdot^c with its derivatives (hrr_node); each output may be null.
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_chem_at(StepArgs a, int n, const double *rho_in, const double *T_in,
+                                                        double *rho_dot, double *hdot, double *dT_out,
+                                                        double *drho_out, double *dA_out)
+{
+    __shared__ double sh_act[M * LBMK_BLOCK];
+    __shared__ double sh_g[M * LBMK_BLOCK];
+    __shared__ WReal sh_w[M * LBMK_BLOCK];
+    const MechConst &mc = c_mech[a.slot];
+    const int t = threadIdx.x, i = blockIdx.x * LBMK_BLOCK + t;
+    if (i >= n) return;
+    double rho_a[M], conc[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        rho_a[s] = rho_in[(size_t)s * n + i];
+        conc[s] = rho_a[s] * mc.invW[s];
+    }
+    const double T = T_in[i];
+    if (rho_dot) {
+        molar_production<M>(mc, T, conc, sh_act, sh_g, sh_w, t, LBMK_BLOCK);
+#pragma unroll
+        for (int s = 0; s < M; ++s) rho_dot[(size_t)s * n + i] = mc.W[s] * (double)sh_w[s * LBMK_BLOCK + t];
+    }
+    if (hdot || dT_out || drho_out || dA_out) {
+        double dT, drho[M], dA[LBMK_MAXR];
+        for (int k = 0; k < mc.R; ++k) dA[k] = 0.0;
+        const double h = hrr_node<M>(mc, T, rho_a, &dT, drho, dA, 1);
+        if (hdot) hdot[i] = h;
+        if (dT_out) dT_out[i] = dT;
+        if (drho_out)
+#pragma unroll
+            for (int s = 0; s < M; ++s) drho_out[(size_t)s * n + i] = drho[s];
+        if (dA_out)
+            for (int k = 0; k < mc.R; ++k) dA_out[(size_t)k * n + i] = dA[k];
+    }
+}
+
+// Temperatures of n given node states (Y [M][n], specific internal energy
+// e [n], Newton starting points T0 [n]; device) by the step's Newton
+// iteration (mixture_energy_poly, solve_T).
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_temperature_at(StepArgs a, int n, const double *Y_in,
+                                                               const double *e_in, const double *T0_in,
+                                                               double *T_out)
+{
+    const MechConst &mc = c_mech[a.slot];
+    const int i = blockIdx.x * LBMK_BLOCK + threadIdx.x;
+    if (i >= n) return;
+    double Y[M], eu[6];
+#pragma unroll
+    for (int s = 0; s < M; ++s) Y[s] = Y_in[(size_t)s * n + i];
+    mixture_energy_poly<M>(mc, Y, eu);
+    T_out[i] = solve_T(eu, e_in[i], T0_in[i], a.status);
+}
+
+// Column c of nb partial records of width w, summed in a fixed order.
+__global__ void __launch_bounds__(LBMK_HRR_THREADS) k_hrr_final(const double *partial, int nb, int w, double *out)
+{
+    __shared__ double sh[LBMK_HRR_THREADS];
+    const int t = threadIdx.x, c = blockIdx.x;
+    double acc = 0.0;
+    for (int b = t; b < nb; b += LBMK_HRR_THREADS) acc += partial[(size_t)b * w + c];
+    sh[t] = acc;
+    __syncthreads();
+    for (int h = LBMK_HRR_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h) sh[t] += sh[t + h];
+        __syncthreads();
+    }
+    if (t == 0) out[c] = sh[0];
+}
+
+// partial: LBMK_HRR_BLOCKS (1 + R) doubles; out: 1 + R doubles
+// {sum hdot^c, sum d hdot^c/d ln A_k}.
+template <int M>
+int run_hrr(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out)
+{
+    if (a.bc_x == 1) {
+        const int plane = a.ny * a.nz;
+        k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
+    }
+    const int nb = (int)std::min<long long>(LBMK_HRR_BLOCKS, ((long long)a.N + LBMK_HRR_THREADS - 1) /
+                                                                 LBMK_HRR_THREADS);
+    k_hrr<M><<<nb, LBMK_HRR_THREADS, 0, a.stream>>>(a, dT, drho, partial);
+    k_hrr_final<<<1 + R, LBMK_HRR_THREADS, 0, a.stream>>>(partial, nb, 1 + R, out);
+    return (int)cudaGetLastError();
+}
+
+template <int M>
+int run_chem_at(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
+                double *dT, double *drho, double *dA)
+{
+    if (n > 0)
+        k_chem_at<M><<<grid_for(n), LBMK_BLOCK, 0, a.stream>>>(a, n, rho_a, T, rho_dot, hdot, dT, drho, dA);
+    return (int)cudaGetLastError();
+}
+
+template <int M>
+int run_temperature_at(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T)
+{
+    if (n > 0) k_temperature_at<M><<<grid_for(n), LBMK_BLOCK, 0, a.stream>>>(a, n, Y, e, T0, T);
     return (int)cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ LBM_MIXED = 1
 LBM_MIXED_FAST = 2
 LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2, 4, 8, 16, 32, 64
 LBM_F_RHO_DOT = 128
+LBM_F_HRR = 256
 LBM_PHASES = 6
 
 _dp = C.POINTER(C.c_double)
@@ -84,6 +85,9 @@ _lib.lbm_moments.argtypes = [C.c_void_p, C.c_uint, C.c_void_p]
 _lib.lbm_moments_count.argtypes = [C.c_void_p, C.c_uint]
 _lib.lbm_moments_count.restype = C.c_size_t
 _lib.lbm_get_populations.argtypes = [C.c_void_p, _dp]
+_lib.lbm_heat_release.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_void_p]
+_lib.lbm_chemistry_at.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 7
+_lib.lbm_temperature_at.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 4
 _lib.lbm_state_buffer.argtypes = [C.c_void_p]
 _lib.lbm_state_buffer.restype = C.c_void_p
 _lib.lbm_destroy.argtypes = [C.c_void_p]
@@ -96,7 +100,8 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
-            "lbm_set_references", "lbm_autotune", "lbm_set_blocks"]
+            "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
+            "lbm_chemistry_at", "lbm_temperature_at"]
 
 
 def library_path() -> str:
@@ -187,6 +192,27 @@ def lbm_moments_count(ctx, mask: int) -> int:
     return _lib.lbm_moments_count(ctx, C.c_uint(mask))
 
 
+def lbm_heat_release(ctx, J: np.ndarray, dlogA, dT_ptr, drho_ptr) -> int:
+    """J: float64 [1] host; dlogA: float64 [R] host or None; dT_ptr,
+    drho_ptr: host or device addresses, or None."""
+    assert J.dtype == np.float64 and J.size >= 1
+    if dlogA is not None:
+        assert dlogA.dtype == np.float64 and dlogA.flags.c_contiguous
+    return _lib.lbm_heat_release(ctx, J.ctypes.data_as(_dp), dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
+                                 C.c_void_p(dT_ptr) if dT_ptr else None, C.c_void_p(drho_ptr) if drho_ptr else None)
+
+
+def lbm_chemistry_at(ctx, n: int, rho_a_ptr: int, T_ptr: int, rho_dot_ptr=None, hdot_ptr=None, dT_ptr=None,
+                     drho_ptr=None, dlogA_ptr=None) -> int:
+    """Device addresses; outputs may be None."""
+    v = [C.c_void_p(p) if p else None for p in (rho_a_ptr, T_ptr, rho_dot_ptr, hdot_ptr, dT_ptr, drho_ptr, dlogA_ptr)]
+    return _lib.lbm_chemistry_at(ctx, int(n), *v)
+
+
+def lbm_temperature_at(ctx, n: int, Y_ptr: int, e_ptr: int, T0_ptr: int, T_ptr: int) -> int:
+    return _lib.lbm_temperature_at(ctx, int(n), *[C.c_void_p(p) if p else None for p in (Y_ptr, e_ptr, T0_ptr, T_ptr)])
+
+
 def lbm_get_populations(ctx, out: np.ndarray) -> int:
     assert out.dtype == np.float64 and out.flags.c_contiguous
     return _lib.lbm_get_populations(ctx, out.ctypes.data_as(_dp))
@@ -255,6 +281,7 @@ class Solver:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.M = species.M
+        self.R = mech.R
         self.S = self.M + 1
         self.N = lattice.nx * lattice.ny * lattice.nz
         self.precision = precision
@@ -400,7 +427,7 @@ class Solver:
         res, row, N, M = {}, 0, self.N, self.M
         for bit, name, rows in ((LBM_F_RHO_A, "rho_a", M), (LBM_F_RHOU, "rhou", 3), (LBM_F_RHOE, "rhoE", 1),
                                 (LBM_F_T, "T", 1), (LBM_F_P, "P", 1), (LBM_F_Y, "Y", M), (LBM_F_J_A, "j_a", 3 * M),
-                                (LBM_F_RHO_DOT, "rho_dot", M)):
+                                (LBM_F_RHO_DOT, "rho_dot", M), (LBM_F_HRR, "hrr", 1)):
             if mask & bit:
                 blk = out[row * N:(row + rows) * N]
                 res[name] = blk.reshape(rows, N) if rows > 1 else blk.reshape(N)
@@ -408,6 +435,66 @@ class Solver:
         if "j_a" in res:
             res["j_a"] = res["j_a"].reshape(M, 3, N)
         return res
+
+    @_on_device
+    def heat_release(self, gradients: bool = True, device: bool = False):
+        """J = sum over nodes of the heat release rate at the current state,
+        and (gradients) dJ/d ln A_k [R], d hdot^c/dT [N], d hdot^c/d rho_a
+        [M, N] there (see lbm_heat_release); the per-node fields as numpy
+        arrays, or torch tensors on the device with device=True."""
+        J = np.zeros(1)
+        if not gradients:
+            _check(lbm_heat_release(self.ctx, J, None, None, None), "lbm_heat_release")
+            return float(J[0])
+        R = self.R
+        dA = np.zeros(R)
+        if device:
+            torch = self.torch
+            dT = torch.empty(self.N, dtype=torch.float64, device=self.device)
+            dr = torch.empty((self.M, self.N), dtype=torch.float64, device=self.device)
+            _check(lbm_heat_release(self.ctx, J, dA, dT.data_ptr(), dr.data_ptr()), "lbm_heat_release")
+        else:
+            dT = np.empty(self.N)
+            dr = np.empty((self.M, self.N))
+            _check(lbm_heat_release(self.ctx, J, dA, dT.ctypes.data, dr.ctypes.data), "lbm_heat_release")
+        return float(J[0]), dA, dT, dr
+
+    @_on_device
+    def chemistry_at(self, rho_a, T):
+        """The step's chemistry at given node states: rho_a [M, n], T [n]
+        (numpy).  Returns a dict of numpy arrays: rho_dot [M, n], hdot [n],
+        dT [n], drho [M, n], dlogA [R, n]."""
+        torch = self.torch
+        rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        n = T.size
+        dev = self.device
+        ri = torch.from_numpy(rho_a).to(dev)
+        ti = torch.from_numpy(T).to(dev)
+        out = {"rho_dot": torch.empty((self.M, n), dtype=torch.float64, device=dev),
+               "hdot": torch.empty(n, dtype=torch.float64, device=dev),
+               "dT": torch.empty(n, dtype=torch.float64, device=dev),
+               "drho": torch.empty((self.M, n), dtype=torch.float64, device=dev),
+               "dlogA": torch.empty((max(self.R, 1), n), dtype=torch.float64, device=dev)}
+        _check(lbm_chemistry_at(self.ctx, n, ri.data_ptr(), ti.data_ptr(), out["rho_dot"].data_ptr(),
+                                out["hdot"].data_ptr(), out["dT"].data_ptr(), out["drho"].data_ptr(),
+                                out["dlogA"].data_ptr()), "lbm_chemistry_at")
+        res = {k: v.cpu().numpy() for k, v in out.items()}
+        res["dlogA"] = res["dlogA"][:self.R]
+        return res
+
+    @_on_device
+    def temperature_at(self, Y, e, T_guess):
+        """The step's Newton temperature at given (Y [M, n], e [n]) from T_guess [n]."""
+        torch = self.torch
+        dev = self.device
+        Yt = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float64)).to(dev)
+        et = torch.from_numpy(np.ascontiguousarray(e, dtype=np.float64)).to(dev)
+        t0 = torch.from_numpy(np.ascontiguousarray(T_guess, dtype=np.float64)).to(dev)
+        T = torch.empty_like(et)
+        _check(lbm_temperature_at(self.ctx, et.numel(), Yt.data_ptr(), et.data_ptr(), t0.data_ptr(), T.data_ptr()),
+               "lbm_temperature_at")
+        return T.cpu().numpy()
 
     @_on_device
     def populations(self) -> np.ndarray:

@@ -1,0 +1,184 @@
+"""Heat release rate hdot^c = -sum_a H_a rho_dot_a (Sec. 5b) and its
+sensitivities on the GPU, against the oracle.
+
+* Node functions (lbm_chemistry_at) on seeded node states that both sides
+  receive unchanged (workload.node_states: 700-2600 K, trace species over
+  six decades, some species absent): the step's production rates against
+  the oracle's rate function, hdot^c against the oracle's, and the
+  derivatives in T, rho_a and ln A_k against central differences of the
+  oracle (tests/hrr_fd.py).  Bars: rates 1e-10 of each species' largest
+  (2e-6 with the fast mixed unit's float exponentials), hdot^c 1e-10 of the
+  largest, derivatives 1e-6 of the largest of each kind (the differences
+  carry ~1e-9).
+* The state entry point (lbm_heat_release): its per-node derivatives equal
+  the node functions at the state's own moments, its totals equal the sums
+  of the per-node values and of the LBM_F_HRR moment row, and they repeat
+  bit for bit.
+* Against the oracle's own lattice after steps (FP64): J and dJ/d ln A_k.
+* At the 256^3 size that bench.py times, after initialisation: sampled
+  nodes against the oracle's state of the same node (tests/oracle_patch.py).
+"""
+import numpy as np
+import pytest
+
+import hrr_fd
+import oracle_patch
+import workload as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2101_01702_gb300 import build
+    build.build()
+    from paper_2101_01702_gb300 import lbm as L
+    return L
+
+
+def _mode(lbm, name):
+    return {"fp64": lbm.LBM_FP64, "mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST}[name]
+
+
+def _tiny_solver(lbm, sp, mech, mode):
+    from workload.problem import InitFields, LatticeSpec, Problem
+    lat = LatticeSpec(5, 4, 3)
+    N = lat.n_nodes
+    X = np.tile((w.configs.PHI1_X + 1e-3)[:, None] / (1 + 9e-3), (1, N))
+    prob = Problem("tiny", lat, sp, mech, InitFields(X=X, T=np.full(N, 1200.0), u=None, P=mech.P0))
+    return lbm.Solver.from_problem(prob, precision=_mode(lbm, mode))
+
+
+def _max_rel(got, ref):
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+@pytest.mark.parametrize("mode,rate_tol", [("fp64", 1e-10), ("mixed", 1e-10), ("mixed_fast", 2e-6)])
+def test_node_functions_against_oracle(orc, lbm, mode, rate_tol):
+    sp, mech = w.mech9()
+    rho_a, T = w.node_states(sp.M, 700, seed=11)
+    s = _tiny_solver(lbm, sp, mech, mode)
+    g = s.chemistry_at(rho_a, T)
+    s.close()
+    o = hrr_fd.oracle_of(orc, sp, mech)
+    rates = np.array([o.rates(rho_a[:, i], T[i]) for i in range(T.size)]).T
+    for a in range(sp.M):
+        scale = np.abs(rates[a]).max()
+        if scale == 0.0:                       # a species no reaction involves
+            assert np.abs(g["rho_dot"][a]).max() == 0.0
+            continue
+        assert np.abs(g["rho_dot"][a] - rates[a]).max() <= rate_tol * scale, a
+    h = hrr_fd.hdot(o, rho_a, T)
+    assert np.abs(h).max() > 0 and _max_rel(g["hdot"], h) <= 1e-10
+    assert _max_rel(g["dT"], hrr_fd.d_dT(o, rho_a, T)) <= 1e-6
+    fd = hrr_fd.d_drho(o, rho_a, T)
+    for a in range(sp.M):
+        scale = max(np.abs(fd[a]).max(), 1e-300)
+        assert np.abs(g["drho"][a] - fd[a]).max() <= 1e-6 * scale, a
+    fdA = hrr_fd.d_dlogA(orc, sp, mech, rho_a, T)
+    assert np.abs(g["dlogA"] - fdA).max() <= 1e-6 * np.abs(fdA).max()
+
+
+def test_log_A_derivatives_sum_to_hdot_without_falloff(lbm):
+    """With every reaction elementary or third-body, hdot^c is a sum of
+    terms each proportional to one A_k, so sum_k d hdot^c/d ln A_k =
+    hdot^c (Euler's relation for homogeneous functions)."""
+    sp, mech = w.mech9()
+    fall = mech.rtype == 2
+    mech.rtype = np.where(fall, 1, mech.rtype).astype(np.int32)
+    rho_a, T = w.node_states(sp.M, 300, seed=12)
+    s = _tiny_solver(lbm, sp, mech, "fp64")
+    g = s.chemistry_at(rho_a, T)
+    s.close()
+    assert fall.any()
+    terms = np.abs(g["dlogA"]).sum(axis=0)                 # sum_k |dH_k q_k| per state
+    assert np.all(np.abs(g["dlogA"].sum(axis=0) - g["hdot"]) <= 1e-13 * terms)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_fast"])
+def test_state_entry_point_matches_node_functions(lbm, mode):
+    prob = w.sphere3d_problem(shape=(21, 18, 17), radius=5.0)
+    s = lbm.Solver.from_problem(prob, precision=_mode(lbm, mode))
+    s.step(3)
+    J, dA, dT, dr = s.heat_release()
+    J2, dA2, dT2, dr2 = s.heat_release()
+    assert J == J2 and np.array_equal(dA, dA2) and np.array_equal(dT, dT2) and np.array_equal(dr, dr2)
+    dTd = s.heat_release(device=True)[2]
+    assert np.array_equal(dTd.cpu().numpy(), dT)
+    assert s.heat_release(gradients=False) == J
+    m = s.moments(lbm.LBM_F_RHO_A | lbm.LBM_F_T | lbm.LBM_F_HRR)
+    g = s.chemistry_at(m["rho_a"], m["T"])
+    s.close()
+    np.testing.assert_allclose(dT, g["dT"], rtol=1e-13, atol=1e-13 * np.abs(g["dT"]).max())
+    np.testing.assert_allclose(dr, g["drho"], rtol=1e-13, atol=1e-13 * np.abs(g["drho"]).max())
+    habs = np.abs(g["hdot"]).sum()
+    assert abs(J - g["hdot"].sum()) <= 1e-12 * habs
+    np.testing.assert_allclose(dA, g["dlogA"].sum(axis=1), rtol=0, atol=1e-12 * np.abs(g["dlogA"]).sum())
+    # the moment row evaluates the rates as the step does (float accumulation
+    # of the reaction contributions in the fast mixed unit)
+    tol = 1e-6 if mode == "mixed_fast" else 1e-10
+    assert abs(m["hrr"].sum() - J) <= tol * habs
+    assert np.abs(m["hrr"] - g["hdot"]).max() <= tol * np.abs(g["hdot"]).max()
+
+
+def test_fp64_lattice_against_oracle(orc, lbm):
+    """J and dJ/d ln A_k of the state after 4 steps, each side from its own
+    run of the same problem."""
+    prob = w.sphere3d_problem(shape=(14, 12, 10), radius=4.0)
+    o = orc.Oracle.from_problem(prob)
+    assert o.step(4) == 0
+    m = o.moments()
+    s = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    s.step(4)
+    J, dA, _, _ = s.heat_release()
+    s.close()
+    one = hrr_fd.oracle_of(orc, prob.species, prob.mech)
+    h = hrr_fd.hdot(one, m["rho_a"], m["T"])
+    assert abs(J - h.sum()) <= 1e-9 * np.abs(h).sum()
+    fdA = hrr_fd.d_dlogA(orc, prob.species, prob.mech, m["rho_a"], m["T"]).sum(axis=1)
+    assert np.abs(dA - fdA).max() <= 1e-6 * np.abs(fdA).max()
+
+
+@pytest.mark.parametrize("mode,tol", [("mixed", 1e-4), ("fp64", 1e-9)])
+def test_fullsize_sampled_nodes_after_init(orc, lbm, mode, tol):
+    """256^3, nine species, right after lbm_init: hdot^c (LBM_F_HRR) and
+    d hdot^c/dT at 300 sampled nodes (uniform, plus the hot kernel and its
+    edge) against the oracle's own state of each node.  In the mixed mode
+    the stored state carries the float rounding of the moving populations,
+    hence its bar."""
+    import torch
+    prob = w.sphere3d_problem(n=256, radius=20.0)
+    s = lbm.Solver.from_problem(prob, precision=_mode(lbm, mode))
+    rng = np.random.default_rng(21)
+    N = prob.lattice.n_nodes
+    is_hot = prob.init.T > 1000.0
+    hot = np.flatnonzero(is_hot)
+    edge = np.flatnonzero(~is_hot & (np.roll(is_hot, 1) | np.roll(is_hot, -1)))   # beside the kernel in x
+    nodes = np.concatenate([rng.choice(N, 100, replace=False), rng.choice(hot, 100, replace=False),
+                            rng.choice(edge, 100, replace=False)])
+    J, dA, dT, _ = s.heat_release(device=True)
+    m = s.moments(lbm.LBM_F_HRR, device=True)
+    idx = torch.from_numpy(nodes).to(dT.device)
+    got_h = m["hrr"][idx].cpu().numpy()
+    got_dT = dT[idx].cpu().numpy()
+    hsum = float(m["hrr"].sum().item())
+    habs = float(m["hrr"].abs().sum().item())
+    del m, dT
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    assert abs(hsum - J) <= 1e-10 * habs
+    one = hrr_fd.oracle_of(orc, prob.species, prob.mech)
+    ref_h, ref_dT = [], []
+    for n in nodes:
+        st = oracle_patch.node_state_after_init(orc, prob, int(n))
+        R1, T1 = st["rho_a"][:, None], np.array([st["T"]])
+        ref_h.append(hrr_fd.hdot(one, R1, T1)[0])
+        ref_dT.append(hrr_fd.d_dT(one, R1, T1)[0])
+    ref_h, ref_dT = np.array(ref_h), np.array(ref_dT)
+    assert np.abs(ref_h).max() > 0
+    assert _max_rel(got_h, ref_h) <= tol
+    assert _max_rel(got_dT, ref_dT) <= max(tol, 1e-6)

@@ -148,26 +148,49 @@ def test_mixed_config1_against_oracle(orc, lbm, mode):
     assert max(err.values()) <= 1e-4, err
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-10), ("mixed_fast", 2e-6)])
-def test_production_rates_against_oracle(orc, lbm, precision, tol):
-    """rho_dot_a (Eq. (sumRhoDot)) from lbm_moments at the GPU's own (rho_a, T)
-    on a burning 1D flame, against the oracle's rate function at the same
-    state, on 600 sampled nodes across the front.  Each species is
-    normalised by its largest rate.  Both FP64 and the mixed mode evaluate
-    the rates in double; the fast mixed bar covers its float 2^f in the
-    exponentials of the rate expressions (relative error ~3e-7) and float
-    accumulation of the reaction contributions."""
+@pytest.fixture(scope="module")
+def oracle_flame60(orc):
+    """The oracle's own 1D flame (512 x 4 x 4) after 60 steps: its moments
+    at 600 nodes sampled across the front, and an oracle of the problem."""
     prob = w.flame1d_problem(nx=512)
-    p = _mode(lbm, precision)
-    s = lbm.Solver.from_problem(prob, precision=p)
-    s.step(60)
-    m = s.moments(lbm.LBM_F_RHO_A | lbm.LBM_F_T | lbm.LBM_F_RHO_DOT)
+    o = orc.Oracle.from_problem(prob)
+    assert o.step(60) == 0
+    m = o.moments()
+    nodes = np.random.default_rng(7).choice(m["T"].size, 600, replace=False)
+    pick = {k: np.ascontiguousarray(m[k][..., nodes]) for k in ("rho_a", "rhou", "rhoE", "T")}
+    return prob, o, pick
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_fast"])
+def test_newton_temperature_against_oracle(oracle_flame60, lbm, precision):
+    """The step's Newton iteration (Eq. (temperature), lbm_temperature_at)
+    at the oracle's flame states, from a start 10 % off, against the
+    oracle's temperatures of those states: 1e-12."""
+    prob, _, m = oracle_flame60
+    rho = m["rho_a"].sum(axis=0)
+    e = m["rhoE"] / rho - 0.5 * (m["rhou"] ** 2).sum(axis=0) / rho ** 2
+    s = lbm.Solver.from_problem(prob, precision=_mode(lbm, precision))
+    T = s.temperature_at(m["rho_a"] / rho, e, 1.1 * m["T"])
     s.close()
-    o = orc.Oracle.from_problem(prob, init=False)
-    rng = np.random.default_rng(7)
-    nodes = rng.choice(m["T"].size, 600, replace=False)
-    ref = np.array([o.rates(m["rho_a"][:, n], m["T"][n]) for n in nodes]).T
-    got = m["rho_dot"][:, nodes]
+    assert np.all(np.abs(T - m["T"]) <= 1e-12 * m["T"])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-10), ("mixed_fast", 2e-6)])
+def test_production_rates_against_oracle(oracle_flame60, lbm, precision, tol):
+    """rho_dot_a (Eq. (sumRhoDot)) as each precision unit's step evaluates
+    it (lbm_chemistry_at), on states of a burning 1D flame: 600 nodes sampled
+    across the front of the oracle's own run (60 steps), against the oracle's
+    rate function at the same states.  Each species is normalised by its
+    largest rate.  Both FP64 and the mixed mode evaluate the rates in
+    double; the fast mixed bar covers its float 2^f in the exponentials of
+    the rate expressions (relative error ~3e-7) and float accumulation of
+    the reaction contributions."""
+    prob, o, m = oracle_flame60
+    rho_a, T = m["rho_a"], m["T"]
+    ref = np.array([o.rates(rho_a[:, i], T[i]) for i in range(T.size)]).T
+    s = lbm.Solver.from_problem(prob, precision=_mode(lbm, precision))
+    got = s.chemistry_at(rho_a, T)["rho_dot"]
+    s.close()
     assert np.abs(ref).max() > 0
     for a in range(ref.shape[0]):
         scale = np.abs(ref[a]).max()
