@@ -44,6 +44,9 @@ FP64_FLOPS_PER_NODE = {
     "mixed_fast": {"k_pre": 723.0, "k_chem": 646.0, "k_step_g": 165.0, "k_step": 18.0},
     "fp64": {"k_pre": 2859.4, "k_chem": 1172.0, "k_step_g": 737.0, "k_step": 12534.0},
 }
+# lbm_heat_release (k_hrr: moments, temperature, hdot^c and its derivatives
+# per node), counted the same way; None until counted.
+HRR_FLOPS_PER_NODE = {"mixed": 3105.9, "mixed_fast": None, "fp64": None}
 DRAM_BYTES_PER_NODE = {
     "mixed": {"k_pre": 2105.5, "k_chem": 64.9, "k_step_g": 600.3, "k_step": 2401.8},
     "mixed_fast": {"k_pre": 2275.2, "k_chem": 64.5, "k_step_g": 600.5, "k_step": 2401.9},
@@ -266,6 +269,42 @@ def run_ours(args):
                     "unit": "GB/s", "frac": step_frac, "algorithmic_bytes_per_node": alg_bytes_node,
                     "peak_source": peak_kind}
 
+    # ---- heat-release objective and its sensitivities ---------------------
+    # lbm_heat_release on the state the timed steps left: hdot^c summed over
+    # the lattice, dJ/d ln A_k, and the per-node derivatives in T and rho_a
+    # (device outputs).  Outside the timed step region.
+    hrr = None
+    if not args.skip_hrr:
+        dT = torch.empty(N, dtype=torch.float64, device=stream.device)
+        dr = torch.empty((M, N), dtype=torch.float64, device=stream.device)
+        J = np.zeros(1)
+        dA = np.zeros(prob.mech.R)
+
+        def hrr_call():
+            st = lbm.lbm_heat_release(s.ctx, J, dA, dT.data_ptr(), dr.data_ptr())
+            if st != lbm.LBM_OK:
+                raise lbm.LBMError(st, "lbm_heat_release")
+
+        hrr_call()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            hrr_call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_hrr = e0.elapsed_time(e1) / reps
+        hrr = {"ms": t_hrr, "mnodes_per_s": N / (t_hrr * 1e-3) / 1e6, "J": float(J[0]),
+               "outputs": "J, dJ/dlnA_k (R), d hdot/dT (N), d hdot/d rho_a (M x N) on the device"}
+        f_h = HRR_FLOPS_PER_NODE.get(args.precision)
+        if f_h:
+            hrr["fp64_tflops"] = f_h * N / (t_hrr * 1e-3) / 1e12
+            hrr["fp64_frac"] = hrr["fp64_tflops"] / FP64_PEAK_TFLOPS
+            hrr["flops_per_node"] = f_h
+        del dT, dr
+        torch.cuda.empty_cache()
+
     # ---- end to end through the C ABI with host buffers ------------------
     e2e = None
     if not args.skip_e2e:
@@ -351,6 +390,7 @@ def run_ours(args):
             "autotuned_blocks": blocks,
             "mixed_fast_step": fast,
             "fp64_step": fp64,
+            "heat_release": hrr,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -516,6 +556,7 @@ def main():
     ap.add_argument("--skip-autotune", action="store_true", help="keep the default launch shapes (profiling runs)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-hrr", action="store_true", help="skip the heat-release sensitivity measurement")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="instead of timing: field error of the mixed modes against double after this many steps")

@@ -165,7 +165,7 @@ int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, do
 // heat release rate and its sensitivities of the state in src (lbm_heat_release):
 // dT [N] and drho [M][N] (device, or null), partial LBMK_HRR_BLOCKS (1 + R)
 // doubles of scratch, out {sum hdot^c, sum d hdot^c/d ln A_k (R)}
-#define LBMK_HRR_BLOCKS 1024
+#define LBMK_HRR_BLOCKS 912     // 6 per SM of 152: whole waves at 2 or 3 resident blocks per SM
 int hrr_fp64(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
 int hrr_mixed(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
 int hrr_mixed_fast(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);

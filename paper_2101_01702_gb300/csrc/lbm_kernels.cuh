@@ -1710,6 +1710,7 @@ __device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const 
 {
     const double invT = 1.0 / T, lnTr = log(T) - mc.log_T_ref;
     const double lnc0 = log(mc.P0_over_r * invT);              // ln(P0/(r T))
+    const double vhf = invT * invT / mc.r_lat;                 // 1/(r T^2), van 't Hoff factor
     double conc[M], WH[M], Wcp[M], g[M], dc[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
@@ -1745,7 +1746,7 @@ __device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const 
         double kr = 0.0, dlnkr = 0.0;
         if (mc.rev[k]) {
             kr = exp_table(lnkf - fma((double)mc.dn[k], lnc0, -dG));       // k_f / K_c
-            dlnkr = dlnkf - (dH * invT * invT / mc.r_lat - mc.dn[k] * invT);
+            dlnkr = dlnkf - fma(dH, vhf, -mc.dn[k] * invT);
         }
         const double qf = kf * Pf, qr = kr * Pp, q0 = qf - qr;
         double F = 1.0, dFdT = 0.0, dFdcM = 0.0, sA = 1.0;
@@ -1798,7 +1799,7 @@ __device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const 
 }
 
 template <int M>
-__global__ void __launch_bounds__(LBMK_HRR_THREADS) k_hrr(StepArgs a, double *dT_out, double *drho_out,
+__global__ void __launch_bounds__(LBMK_HRR_THREADS, 3) k_hrr(StepArgs a, double *dT_out, double *drho_out,
                                                           double *partial)
 {
     __shared__ double sh_dA[LBMK_MAXR * LBMK_HRR_THREADS];
