@@ -84,6 +84,19 @@ typedef double WReal;
 #ifndef LBMK_STEP_MINB
 #define LBMK_STEP_MINB (LBMK_MIXED ? 3 : 1)
 #endif
+// The moments of lbm_moments (outside the step), 256^3 mixed, T and Y:
+// 44.0 ms at 178 registers (2 blocks per SM), 29.3 ms at 4 blocks, 23.8 ms
+// at 5 (96 registers, ~200 B spilled); the double unit stays unconstrained
+// (a cap of 128 registers spills 600 B there).
+#ifndef LBMK_MOM_MINB
+#define LBMK_MOM_MINB (LBMK_MIXED ? 5 : 1)
+#endif
+// Initialisation (equilibria of every set, outside the step; FP64-bound and
+// insensitive to occupancy: 43.1-43.5 ms at 4 or 6 blocks per SM): 6 blocks
+// (80 registers, ~30 B spilled).
+#ifndef LBMK_INIT_MINB
+#define LBMK_INIT_MINB 6
+#endif
 #if LBMK_MIXED
 #define INVWWD(a_, b_) (mc.inv_WWD_f[a_][b_])
 #define RA(a_) (mc.Ra_f[a_])
@@ -568,7 +581,7 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
 // Initialisation: every set at equilibrium for X, T, u and pressure P.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_init(StepArgs a, const double *X, const double *Tf,
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_INIT_MINB) k_init(StepArgs a, const double *X, const double *Tf,
                                                      const double *uf, double P)
 {
     const MechConst &mc = c_mech[a.slot];
@@ -831,7 +844,7 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
 // Moments for lbm_moments: the fields of the state in src (no record).
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_moments(StepArgs a, unsigned mask, double *out)
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_MOM_MINB) k_moments(StepArgs a, unsigned mask, double *out)
 {
     __shared__ double sh_act[M * LBMK_BLOCK];
     __shared__ double sh_g[M * LBMK_BLOCK];

@@ -65,6 +65,29 @@ def test_batch_equals_single_flames_bitwise_fp64(lbm):
             assert np.array_equal(_segment(mb[name], prob, k), m1[name]), (k, name)
 
 
+def test_batch_heat_release_equals_single_flames(lbm):
+    """lbm_heat_release on a batch: the per-node derivatives of each flame
+    are those of the flame alone, bit for bit (double precision), and J and
+    dJ/d ln A_k are the sums over the flames (up to the order of the sums)."""
+    prob = _batch()
+    sb = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    sb.step(60)
+    Jb, dAb, dTb, drb = sb.heat_release()
+    sb.close()
+    Js, dAs, habs = 0.0, 0.0, 0.0
+    for k in range(len(LENGTHS)):
+        s1 = lbm.Solver.from_problem(w.flame_of_batch(prob, k), precision=lbm.LBM_FP64)
+        s1.step(60)
+        J1, dA1, dT1, dr1 = s1.heat_release()
+        h1 = s1.moments(lbm.LBM_F_HRR)["hrr"]
+        s1.close()
+        assert np.array_equal(_segment(dTb, prob, k), dT1), k
+        assert np.array_equal(_segment(drb, prob, k), dr1), k
+        Js, dAs, habs = Js + J1, dAs + dA1, habs + np.abs(h1).sum()
+    assert habs > 0 and abs(Jb - Js) <= 1e-12 * habs
+    assert np.abs(dAb - dAs).max() <= 1e-10 * np.abs(dAs).max()
+
+
 def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
