@@ -70,6 +70,17 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert lib.lbm_strerror(12345) == "unknown status"
 
 
+def test_context_calls_reject_a_null_context_without_touching_the_gpu(lib):
+    raw = C.CDLL(lib.library_path())
+    for name, nargs in (("lbm_heat_release", 5), ("lbm_chemistry_at", 9), ("lbm_temperature_at", 6),
+                        ("lbm_step", 2), ("lbm_step_async", 2), ("lbm_step_graph", 2), ("lbm_sync", 1),
+                        ("lbm_moments", 3), ("lbm_get_populations", 2), ("lbm_destroy", 1)):
+        f = getattr(raw, name)
+        f.argtypes = [C.c_void_p] * nargs
+        f.restype = C.c_int
+        assert f(*([None] * nargs)) == lib.LBM_ERR_ARG, name
+
+
 def test_buffer_sizes_of_a_batch_of_lattices(lib):
     import workload as w
     p = w.sphere3d_problem(n=8, radius=2)

@@ -182,3 +182,25 @@ def test_fullsize_sampled_nodes_after_init(orc, lbm, mode, tol):
     assert np.abs(ref_h).max() > 0
     assert _max_rel(got_h, ref_h) <= tol
     assert _max_rel(got_dT, ref_dT) <= max(tol, 1e-6)
+
+
+def test_node_functions_argument_checks(lbm):
+    """Host pointers and negative counts are rejected before any launch;
+    n = 0 does nothing; the context stays usable."""
+    import torch
+    sp, mech = w.mech9()
+    s = _tiny_solver(lbm, sp, mech, "fp64")
+    rho_h = np.ones((sp.M, 4))
+    T_h = np.full(4, 1000.0)
+    T_d = torch.full((4,), 1000.0, dtype=torch.float64, device="cuda")
+    rho_d = torch.ones((sp.M, 4), dtype=torch.float64, device="cuda")
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    assert lbm.lbm_chemistry_at(s.ctx, 4, rho_h.ctypes.data, T_d.data_ptr(), None, out.data_ptr()) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_chemistry_at(s.ctx, -1, rho_d.data_ptr(), T_d.data_ptr()) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_chemistry_at(s.ctx, 0, None, None) == lbm.LBM_OK
+    assert lbm.lbm_temperature_at(s.ctx, 4, rho_d.data_ptr(), T_h.ctypes.data, T_d.data_ptr(),
+                                  out.data_ptr()) == lbm.LBM_ERR_ARG
+    assert lbm.lbm_chemistry_at(s.ctx, 4, rho_d.data_ptr(), T_d.data_ptr(), None, out.data_ptr()) == lbm.LBM_OK
+    assert np.isfinite(out.cpu().numpy()).all()
+    assert s.step(1) == lbm.LBM_OK
+    s.close()
