@@ -213,8 +213,9 @@ int lbm_step_graph(lbm_ctx *ctx, int n);
  * are bit for bit those of the untuned context.  Allocates and frees one
  * temporary row of N doubles.  block_out (NULL or 6 ints) receives the
  * chosen blocks in launch order: ghost nodes, moments, production rates,
- * gradients, energy collision, species/mixture collision.  Waits for the
- * stream; returns like lbm_sync. */
+ * gradients, energy collision, species/mixture collision (the production-
+ * rate entry has no effect: the rates are formed inside the species
+ * collision).  Waits for the stream; returns like lbm_sync. */
 int lbm_autotune(lbm_ctx *ctx, int trials, int *block_out);
 
 /* Sets the block sizes of the six kernels directly (for instance a choice
@@ -230,7 +231,9 @@ int lbm_set_blocks(lbm_ctx *ctx, const int *blocks);
  * the summed device time of the ghost-node, moment, production-rate,
  * gradient, energy-collision and species/mixture-collision kernels over
  * the n steps, phase_ms[LBM_PHASES] the device time from the first launch
- * to the end of the last.  Returns like lbm_step. */
+ * to the end of the last.  The production rates are formed inside the
+ * species/mixture-collision kernel (no kernel of their own), so their phase
+ * is empty and their time is in phase_ms[5].  Returns like lbm_step. */
 #define LBM_PHASES 6
 int lbm_step_timed(lbm_ctx *ctx, int n, double *phase_ms);
 

@@ -94,6 +94,15 @@ typedef double WReal;
 // Initialisation (equilibria of every set, outside the step; FP64-bound and
 // insensitive to occupancy: 43.1-43.5 ms at 4 or 6 blocks per SM): 6 blocks
 // (80 registers, ~30 B spilled).
+// Production rates formed inside the species collision (k_step) instead of
+// a kernel of their own: in the mixed units k_step waits on memory with
+// the FP64 pipe idle, and the rates are FP64 work of the same node, so the
+// fused kernel overlaps the two (256^3 mixed: k_chem 24.6 ms + k_step
+// 11.9 ms -> 29.5 ms; double: 24.0 + 257.7 -> 274.7 ms).  Results are bit
+// for bit those of the separate kernels (LBMK_FUSE_CHEM=0).
+#ifndef LBMK_FUSE_CHEM
+#define LBMK_FUSE_CHEM 1
+#endif
 #ifndef LBMK_INIT_MINB
 #define LBMK_INIT_MINB 6
 #endif
@@ -1301,6 +1310,11 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
     // thread's column (kept in registers in the mixed units)
     __shared__ double sh_yz[2 * M * LBMK_BLOCK];
 #endif
+#if LBMK_FUSE_CHEM
+    __shared__ double sh_act[M * LBMK_BLOCK];
+    __shared__ double sh_g[M * LBMK_BLOCK];
+    __shared__ WReal sh_w[M * LBMK_BLOCK];
+#endif
     const MechConst &mc = c_mech[a.slot];
     Node nd;
     if (!node_of(nd, a)) return;
@@ -1346,8 +1360,21 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 #pragma unroll
         for (int d = 0; d < 3; ++d) xs[s][d] = u[d] + ld(rr.du + 3 * s + d);
         bt[s] = ld(rr.beta + s);
+#if !LBMK_FUSE_CHEM
         wd[s] = ld(rr.wd + s);
+#endif
     }
+#if LBMK_FUSE_CHEM
+    {
+        // the production rates of this node, as k_chem forms them
+        double conc[M];
+#pragma unroll
+        for (int s = 0; s < M; ++s) conc[s] = (double)rho * (double)Yl[s] * mc.invW[s];
+        molar_production<M>(mc, ldd(DR_T), conc, sh_act, sh_g, sh_w, threadIdx.x, LBMK_BLOCK);
+#pragma unroll
+        for (int s = 0; s < M; ++s) wd[s] = (Real)(mc.W[s] * sh_w[s * LBMK_BLOCK + threadIdx.x]);
+    }
+#endif
     const Real u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
 
     const PopView v = view(a.src, a);
@@ -1517,6 +1544,7 @@ int launch_one(const StepArgs &a, int k)
         break;
     case LBMK_K_PRE: k_pre<M><<<grid_for(a.N, bs), bs, 0, a.stream>>>(a); break;
     case LBMK_K_CHEM: {
+        if (LBMK_FUSE_CHEM) break;          // the rates are formed inside k_step
         // blocks needing more than 48 KB of dynamic shared memory opt in,
         // once per device (only tuned block sizes do; the default never)
         if (chem_smem<M>(bs) > 48 * 1024) {
