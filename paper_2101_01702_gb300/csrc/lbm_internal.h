@@ -30,7 +30,7 @@
 // Storage-type rows:
 //   nup  1/omega - 1/2      phi  Phi (3)        g    G (3)
 //   y    Y_a (M)            rho  rho            u    u (3)
-//   du   du_a (3M, a-major) wd   rho_dot_a (M)  beta beta_a (M)
+//   du   du_a (3M, a-major) wd   rho_dot_a (M; written only by k_chem)  beta beta_a (M)
 //   kappa m R_U T           rt   R T            om   omega      om1 omega_1
 //   p    P                  dq   (omega - omega_1)(q* - q^eq) without the grad-Y part (3)
 //   h    H_a (M)
@@ -107,7 +107,7 @@ struct MechConst {
 };
 
 #define LBMK_BLOCK 128      // default block; the block of k_pre and k_step is at most this
-#define LBMK_MAXBLOCK 256   // largest block of the kernels tuned up to it (k_chem, k_grad, k_step_g)
+#define LBMK_MAXBLOCK 256   // largest block of the kernels tuned up to it (k_grad, k_step_g; k_chem)
 
 // The kernels of one step, in launch order (timing phases and autotuned
 // block sizes are indexed alike).

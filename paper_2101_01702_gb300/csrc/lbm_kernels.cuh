@@ -13,19 +13,22 @@
 // the Stefan-Maxwell system (Eq. (transform1)) and the reaction rates with
 // their equilibrium constants are double precision in every unit.
 //
-// One time step is six launches on one stream:
+// One time step is four launches on one stream (five with x ghosts):
 //   k_ghost  x-face ghost nodes (Sec. 5a; only for non-periodic x)
 //   k_pre    pull, all moments, Newton temperature, relaxation rates,
 //            Stefan-Maxwell diffusion velocities, the local part of the
 //            energy-flux correction and the energy equilibrium moments;
 //            writes the per-node record.
-//   k_chem   production rates of the reaction mechanism (record rows)
 //   k_grad   G_alpha = (1/omega - 1/2) d_alpha Phi_alpha (Eq. (Xalpha))
 //   k_step_g pull of the energy set, sum_a H_a grad Y_a from the neighbours'
 //            records, and the collision of Eq. (g) (double)
-//   k_step   pull of the species and mixture sets, X = -d_alpha G_alpha from
-//            the neighbours' records, and the collisions of
-//            Eqs. (finalNumericalEquations), (f), direction by direction
+//   k_step   production rates of the reaction mechanism at the node
+//            (double), pull of the species and mixture sets,
+//            X = -d_alpha G_alpha from the neighbours' records, and the
+//            collisions of Eqs. (finalNumericalEquations), (f), direction
+//            by direction
+// (k_chem, the production rates as a kernel of their own writing record
+// rows, serves builds with LBMK_FUSE_CHEM=0.)
 // One thread owns one lattice node; populations are structure-of-arrays
 // [set][direction][node] so that a warp's pulls are coalesced rows.
 #pragma once
