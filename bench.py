@@ -158,6 +158,19 @@ def _cpu_oracle_sample(min_seconds: float = 10.0, max_steps: int = 400, warmup: 
             "sample": f"sphere3d 32^3 (radius 8), 9 species / 21 reactions, FP64, {n} steps in {dt:.1f} s"}
 
 
+def _cpu_oracle_single_thread(min_seconds: float = 3.0):
+    """The same sample on one host thread (a child process started with
+    OMP_NUM_THREADS=1, so that this process's thread pool is untouched)."""
+    code = ("import json, bench; r = bench._cpu_oracle_sample(min_seconds=%r, max_steps=100); "
+            "print(json.dumps(r))" % min_seconds)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=str(ROOT), env=env, capture_output=True, text=True,
+                       timeout=120)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -380,6 +393,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = _cpu_oracle_sample()
+        one = _cpu_oracle_single_thread()
+        if one:
+            cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
 
     if rank == 0:
         line = {
