@@ -166,6 +166,16 @@ __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >
 
 __device__ __forceinline__ void flag(unsigned *status, unsigned bit) { atomicOr(status, bit); }
 
+// Tests on the bit pattern (integer pipe; the FP64 pipe is the step's
+// bottleneck): not Inf or NaN, and not +-0.
+__device__ __forceinline__ bool finite_bits(double x) { return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000; }
+__device__ __forceinline__ bool finite_bits(float x) { return (__float_as_int(x) & 0x7f800000) != 0x7f800000; }
+__device__ __forceinline__ bool nonzero_bits(double x)
+{
+    return ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) != 0;
+}
+__device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x) & 0x7fffffff) != 0; }
+
 // Checked builds: records a failed index check; always true otherwise.
 __device__ __forceinline__ bool index_ok(bool ok, unsigned *status)
 {
@@ -963,7 +973,8 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     for (int s = 0; s < M; ++s) {
         Y[s] = rho_a[s] * ir;
         inv_m = fma(Y[s], mc.invW[s], inv_m);
-        neg |= rho_a[s] < -1e-10 * rho;      // below rounding noise of trace species
+        if (__double2hiint(rho_a[s]) < 0)     // sign bit first: the compare only for negative values
+            neg |= rho_a[s] < -1e-10 * rho;  // below rounding noise of trace species
     }
     if (!(rho > 0.0) || !isfinite(sm.rhoE)) flag(a.status, LBMK_BIT_NONFINITE);
     if (neg) flag(a.status, LBMK_BIT_NEGATIVE);
@@ -1046,8 +1057,8 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
             // species (Y_k = 0), whose row and column vanish and whose
             // diffusion velocity is multiplied by Y_k = 0 wherever it is used.
             D[k] = Ln[k][k];
-            if (!isfinite(D[k])) flag(a.status, LBMK_BIT_PIVOT);
-            Dinv[k] = D[k] != (SReal)0 ? (SReal)1 / D[k] : (SReal)0;
+            if (!finite_bits(D[k])) flag(a.status, LBMK_BIT_PIVOT);
+            Dinv[k] = nonzero_bits(D[k]) ? (SReal)1 / D[k] : (SReal)0;
 #pragma unroll
             for (int i = k + 1; i < M; ++i) Ln[i][k] *= Dinv[k];
         }
