@@ -416,7 +416,7 @@ __device__ __forceinline__ double solve_T(const double u[6], double e, double T,
         const double Fp = fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
         const double dT = F / Fp;
         T -= dT;
-        if (!isfinite(T)) { flag(status, LBMK_BIT_NONFINITE); return T; }
+        if (!finite_bits(T)) { flag(status, LBMK_BIT_NONFINITE); return T; }
         if (fabs(dT) <= 1e-13 * fabs(T)) return T;
     }
     flag(status, LBMK_BIT_NEWTON);
