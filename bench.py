@@ -41,7 +41,9 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 #   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
 # The production rates are formed inside k_step (no k_chem launch), so
 # their flops count there (double unit: the sum of the two kernels' counts
-# taken before they were fused; the instructions are the same).
+# taken before they were fused; the instructions are the same).  k_pre was
+# counted before its finiteness and sign checks moved to the integer pipe,
+# which removed compares, not flops.
 FP64_FLOPS_PER_NODE = {
     "mixed": {"k_pre": 2054.4, "k_step_g": 165.0, "k_step": 1189.0},
     "mixed_fast": {"k_pre": 723.0, "k_step_g": 165.0, "k_step": 663.0},
