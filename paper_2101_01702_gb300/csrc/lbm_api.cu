@@ -652,7 +652,7 @@ int lbm_heat_release(lbm_ctx *c, double *J, double *dJ_dlogA, double *dJ_dT, dou
     if (dJ_drho && !dr_dev) { dr = stage + off; off += M * N; }
     off = (off + 31) & ~(size_t)31;
     double *partial = stage + off;
-    off += (size_t)LBMK_HRR_BLOCKS * (1 + R);
+    off += (size_t)lbmk::hrr_blocks(c->N) * (1 + R);
     double *tot = stage + off;
     off += 1 + R;
     if (off * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;

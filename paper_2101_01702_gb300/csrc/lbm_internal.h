@@ -163,9 +163,16 @@ int ref_stats_mixed(const StepArgs &a, const double *X, const double *T, double 
 int ref_stats_mixed_fast(const StepArgs &a, const double *X, const double *T, double P, double *scratch, double *out);
 
 // heat release rate and its sensitivities of the state in src (lbm_heat_release):
-// dT [N] and drho [M][N] (device, or null), partial LBMK_HRR_BLOCKS (1 + R)
+// dT [N] and drho [M][N] (device, or null), partial hrr_blocks(N) (1 + R)
 // doubles of scratch, out {sum hdot^c, sum d hdot^c/d ln A_k (R)}
 #define LBMK_HRR_BLOCKS 912     // 6 per SM of 152: whole waves at 2 or 3 resident blocks per SM
+#define LBMK_HRR_THREADS 128
+// blocks of the heat-release kernel for N nodes (grid-stride beyond)
+inline int hrr_blocks(long long N)
+{
+    const long long b = (N + LBMK_HRR_THREADS - 1) / LBMK_HRR_THREADS;
+    return (int)(b < LBMK_HRR_BLOCKS ? b : LBMK_HRR_BLOCKS);
+}
 int hrr_fp64(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
 int hrr_mixed(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);
 int hrr_mixed_fast(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out);

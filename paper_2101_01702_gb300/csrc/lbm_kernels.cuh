@@ -1769,7 +1769,6 @@ int run_ref_stats(const StepArgs &a, const double *X, const double *T, double P,
 // then a tree in shared memory, in a fixed order); k_hrr_final sums the
 // blocks in a fixed order, so that the totals repeat from run to run.
 // ---------------------------------------------------------------------
-constexpr int LBMK_HRR_THREADS = 128;
 
 // Specific heat C_p,a(T) = dH_a/dT.
 __device__ __forceinline__ double cp_spec(const MechConst &mc, int a, double T)
@@ -2006,7 +2005,7 @@ __global__ void __launch_bounds__(LBMK_HRR_THREADS) k_hrr_final(const double *pa
     if (t == 0) out[c] = sh[0];
 }
 
-// partial: LBMK_HRR_BLOCKS (1 + R) doubles; out: 1 + R doubles
+// partial: hrr_blocks(N) (1 + R) doubles; out: 1 + R doubles
 // {sum hdot^c, sum d hdot^c/d ln A_k}.
 template <int M>
 int run_hrr(const StepArgs &a, int R, double *dT, double *drho, double *partial, double *out)
@@ -2015,8 +2014,7 @@ int run_hrr(const StepArgs &a, int R, double *dT, double *drho, double *partial,
         const int plane = a.ny * a.nz;
         k_ghost<M><<<grid_for(2 * (a.nseg > 1 ? a.nseg : 1) * plane), LBMK_BLOCK, 0, a.stream>>>(a);
     }
-    const int nb = (int)std::min<long long>(LBMK_HRR_BLOCKS, ((long long)a.N + LBMK_HRR_THREADS - 1) /
-                                                                 LBMK_HRR_THREADS);
+    const int nb = lbmk::hrr_blocks(a.N);
     k_hrr<M><<<nb, LBMK_HRR_THREADS, 0, a.stream>>>(a, dT, drho, partial);
     k_hrr_final<<<1 + R, LBMK_HRR_THREADS, 0, a.stream>>>(partial, nb, 1 + R, out);
     return (int)cudaGetLastError();

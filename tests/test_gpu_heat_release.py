@@ -203,4 +203,9 @@ def test_node_functions_argument_checks(lbm):
     assert lbm.lbm_chemistry_at(s.ctx, 4, rho_d.data_ptr(), T_d.data_ptr(), None, out.data_ptr()) == lbm.LBM_OK
     assert np.isfinite(out.cpu().numpy()).all()
     assert s.step(1) == lbm.LBM_OK
+    # a 60-node lattice: one block of partial sums fits the scratch
+    J, dA, dT, dr = s.heat_release()
+    m = s.moments(lbm.LBM_F_RHO_A | lbm.LBM_F_T)
+    g = s.chemistry_at(m["rho_a"], m["T"])
+    assert abs(J - g["hdot"].sum()) <= 1e-12 * np.abs(g["hdot"]).sum()
     s.close()
