@@ -51,3 +51,32 @@ def d_dlogA(orc, species, mech, rho_a, T, h=1e-6):
         lo.log_A[k] -= h
         out[k] = (hdot(oracle_of(orc, species, hi), rho_a, T) - hdot(oracle_of(orc, species, lo), rho_a, T)) / (2 * h)
     return out
+
+
+def hdot_of_state(o, one):
+    """hdot^c at every node of the oracle lattice o's current state (its
+    moments and Newton temperatures), evaluated by the one-node oracle one."""
+    m = o.moments()
+    assert m["status"] == 0
+    return hdot(one, m["rho_a"], m["T"])
+
+
+def d_dpop(o, one, samples, rel=1e-6):
+    """dJ/dF at samples (node, set, direction) of o's state, J = sum of
+    hdot^c: central differences with a step of rel times the largest
+    population of that set at that node.  Only the node that pulls the
+    perturbed population changes, so the per-node differences are summed."""
+    pop = o.get_pop()
+    out = []
+    for (x, s, i) in samples:
+        h = rel * np.abs(pop[x, s]).max()
+        p1 = pop.copy()
+        p1[x, s, i] += h
+        o.set_pop(p1)
+        hp = hdot_of_state(o, one)
+        p1[x, s, i] -= 2 * h
+        o.set_pop(p1)
+        hm = hdot_of_state(o, one)
+        out.append(float((hp - hm).sum() / (2 * h)))
+    o.set_pop(pop)
+    return np.array(out)

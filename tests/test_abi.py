@@ -72,7 +72,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
 
 def test_context_calls_reject_a_null_context_without_touching_the_gpu(lib):
     raw = C.CDLL(lib.library_path())
-    for name, nargs in (("lbm_heat_release", 5), ("lbm_chemistry_at", 9), ("lbm_temperature_at", 6),
+    for name, nargs in (("lbm_heat_release", 5), ("lbm_heat_release_adjoint", 2), ("lbm_chemistry_at", 9), ("lbm_temperature_at", 6),
                         ("lbm_step", 2), ("lbm_step_async", 2), ("lbm_step_graph", 2), ("lbm_sync", 1),
                         ("lbm_moments", 3), ("lbm_get_populations", 2), ("lbm_destroy", 1)):
         f = getattr(raw, name)

@@ -63,3 +63,27 @@ def test_node_states_cover_absent_and_trace_species():
     assert (rho_a == 0).any() and (rho_a > 0).sum(axis=0).min() >= 1
     Y = rho_a / rho_a.sum(axis=0)
     assert Y[Y > 0].min() < 1e-5 and T.min() >= 700.0 and T.max() <= 2600.0
+
+
+def test_energy_population_gradient_is_the_temperature_derivative(orc):
+    """Perturbing an energy population g_i(x) moves only rho E of the node
+    n = x + c_i that pulls it, hence only its temperature, by
+    dT = d(rho E) / (rho C_v): the finite-difference population gradient
+    (tests/hrr_fd.py) equals d hdot^c/dT / (rho C_v) at n."""
+    prob = w.sphere3d_problem(shape=(6, 5, 4), radius=1.5)
+    o = orc.Oracle.from_problem(prob)
+    assert o.step(1) == 0
+    one = hrr_fd.oracle_of(orc, prob.species, prob.mech)
+    m = o.moments()
+    M, nx, ny, nz = prob.species.M, 6, 5, 4
+    x0, y0, z0 = 3, 2, 2
+    for i in (13, 14, 22):          # c = (0,0,0), (1,0,0), (0,0,1); i = (cx+1) + 3 (cy+1) + 9 (cz+1)
+        cx, cy, cz = i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1
+        x = x0 + nx * (y0 + ny * z0)
+        n = (x0 + cx) % nx + nx * ((y0 + cy) % ny + ny * ((z0 + cz) % nz))
+        fd = hrr_fd.d_dpop(o, one, [(x, M, i)])[0]
+        rho_a, T = m["rho_a"][:, n], m["T"][n]
+        rho = rho_a.sum()
+        Cv = float((rho_a / rho * one.thermo(T)["Cv"]).sum())
+        ref = hrr_fd.d_dT(one, rho_a[:, None], np.array([T]))[0] / (rho * Cv)
+        assert ref != 0.0 and abs(fd - ref) <= 1e-5 * abs(ref), (i, fd, ref)
