@@ -281,6 +281,21 @@ size_t lbm_moments_count(const lbm_ctx *ctx, unsigned mask);
  * LBM_ERR_ARG for a NULL ctx or J. */
 int lbm_heat_release(lbm_ctx *ctx, double *J, double *dJ_dlogA, double *dJ_dT, double *dJ_drho);
 
+/* Gradient of the same objective J = sum over the nodes of hdot^c with
+ * respect to the stored populations of the current state: the source term
+ * that J contributes to an adjoint of the step.  Node n pulls
+ * P_si(n) = F_si(n - c_i) and forms rho_a, rho, rho u and rho E; the
+ * temperature depends on them through Eq. (temperature) (implicit function:
+ * dT = (de - sum_a U_a dY_a) / C_v), the slaved density through
+ * Eq. (strongest), and hdot^c on (rho_a, T) as in lbm_heat_release.
+ *   dJ_dF  host or device, double [M+1][27][N] (the layout of
+ *          lbm_get_populations): dJ/dF_si(x) for every set, direction and
+ *          node, with respect to the absolute population values
+ * Periodic lattices only (LBM_ERR_UNSUPPORTED for ghost-node faces or
+ * batches).  The second population buffer serves as scratch.  Waits for
+ * the stream; returns like lbm_sync. */
+int lbm_heat_release_adjoint(lbm_ctx *ctx, double *dJ_dF);
+
 /* The step's chemistry at n given node states, for checks of the node
  * functions on inputs of the caller's choice.  Inputs, device:
  *   rho_a [M][n] species densities, T [n] temperatures.

@@ -67,4 +67,18 @@ int temperature_at_mixed(const StepArgs &a, int n, const double *Y, const double
 #undef CALL
 }
 
+int hrr_adj_mixed(const StepArgs &a, double *adj)
+{
+#define CALL(M_) run_hrr_adj<M_>(a, adj)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
+int hrr_adj_gather_mixed(const StepArgs &a, const double *adj, int s, double *out)
+{
+#define CALL(M_) run_hrr_adj_gather<M_>(a, adj, s, out)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 }  // namespace lbmk

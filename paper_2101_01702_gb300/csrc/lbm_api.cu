@@ -63,13 +63,16 @@ size_t store_size(int precision) { return is_mixed(precision) ? sizeof(float) : 
 const lbmk::PrecisionOps kOps[3] = {
     {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64,
      lbmk::launch_one_fp64, lbmk::hrr_fp64,
-     lbmk::chem_at_fp64, lbmk::temperature_at_fp64},
+     lbmk::chem_at_fp64, lbmk::temperature_at_fp64,
+     lbmk::hrr_adj_fp64, lbmk::hrr_adj_gather_fp64},
     {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed,
      lbmk::launch_one_mixed, lbmk::hrr_mixed,
-     lbmk::chem_at_mixed, lbmk::temperature_at_mixed},
+     lbmk::chem_at_mixed, lbmk::temperature_at_mixed,
+     lbmk::hrr_adj_mixed, lbmk::hrr_adj_gather_mixed},
     {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
      lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast, lbmk::hrr_mixed_fast,
-     lbmk::chem_at_mixed_fast, lbmk::temperature_at_mixed_fast},
+     lbmk::chem_at_mixed_fast, lbmk::temperature_at_mixed_fast,
+     lbmk::hrr_adj_mixed_fast, lbmk::hrr_adj_gather_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -669,6 +672,33 @@ int lbm_heat_release(lbm_ctx *c, double *J, double *dJ_dlogA, double *dJ_dT, dou
     if (dJ_dlogA)
         for (int k = 0; k < R; ++k) dJ_dlogA[k] = htot[1 + k];
     return LBM_OK;
+}
+
+int lbm_heat_release_adjoint(lbm_ctx *c, double *dJ_dF)
+{
+    if (!c || !dJ_dF) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    if (c->lat.bc_x != LBM_BC_PERIODIC || c->nseg > 1) return LBM_ERR_UNSUPPORTED;
+    const size_t N = (size_t)c->N, S = (size_t)c->S, M = (size_t)c->M;
+    const bool dev = is_device_ptr(dJ_dF);
+    // scratch in the free population buffer: the per-node moment
+    // derivatives, then (host output) one set's rows at a time
+    double *adj = (double *)c->buf[1 - c->cur];
+    double *rows = adj + (M + 4) * N;
+    if (((M + 4) * N + (dev ? 0 : LBMK_Q * N)) * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+    const StepArgs a = args_of(c);
+    if (ops(c->lat.precision).hrr_adj(a, adj)) return LBM_ERR_CUDA;
+    for (size_t s = 0; s < S; ++s) {
+        double *target = dev ? dJ_dF + s * LBMK_Q * N : rows;
+        if (ops(c->lat.precision).hrr_adj_gather(a, adj, (int)s, target)) return LBM_ERR_CUDA;
+        if (!dev) {
+            const int st = check_cuda(cudaMemcpyAsync(dJ_dF + s * LBMK_Q * N, rows, LBMK_Q * N * sizeof(double),
+                                                      cudaMemcpyDeviceToHost, c->stream));
+            if (st != LBM_OK) return st;
+        }
+    }
+    return lbm_sync(c);
 }
 
 int lbm_chemistry_at(lbm_ctx *c, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,

@@ -190,6 +190,16 @@ int temperature_at_mixed(const StepArgs &a, int n, const double *Y, const double
 int temperature_at_mixed_fast(const StepArgs &a, int n, const double *Y, const double *e, const double *T0,
                               double *T);
 
+// gradient of sum hdot^c with respect to the populations of src (periodic
+// lattices; lbm_heat_release_adjoint): adj [M + 4][N] per-node moment
+// derivatives, then per set s (0..M) the gathered rows out [27][N]
+int hrr_adj_fp64(const StepArgs &a, double *adj);
+int hrr_adj_mixed(const StepArgs &a, double *adj);
+int hrr_adj_mixed_fast(const StepArgs &a, double *adj);
+int hrr_adj_gather_fp64(const StepArgs &a, const double *adj, int s, double *out);
+int hrr_adj_gather_mixed(const StepArgs &a, const double *adj, int s, double *out);
+int hrr_adj_gather_mixed_fast(const StepArgs &a, const double *adj, int s, double *out);
+
 // one kernel of the step (LBMK_K_*) with the block size a.bs[kernel]
 int launch_one_fp64(const StepArgs &a, int kernel);
 int launch_one_mixed(const StepArgs &a, int kernel);
@@ -207,5 +217,7 @@ struct PrecisionOps {
     int (*chem_at)(const StepArgs &a, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,
                    double *dT, double *drho, double *dA);
     int (*temperature_at)(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T);
+    int (*hrr_adj)(const StepArgs &a, double *adj);
+    int (*hrr_adj_gather)(const StepArgs &a, const double *adj, int s, double *out);
 };
 }  // namespace lbmk

@@ -1779,7 +1779,7 @@ __device__ __forceinline__ double cp_spec(const MechConst &mc, int a, double T)
 
 // hdot^c at one node state (T, rho_a) and its derivatives: d/dT into *dT,
 // d/drho_a into drho[M], and d/d ln A_k added to dA[k * stride] (k < R).
-template <int M>
+template <int M, bool WITH_A = true>
 __device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const double *rho_a, double *dT_out,
                                            double *drho, double *dA, int stride)
 {
@@ -1844,7 +1844,7 @@ __device__ __forceinline__ double hrr_node(const MechConst &mc, double T, const 
         }
         const double q = F * q0;
         hdot -= dH * q;
-        dA[k * stride] -= dH * q * sA;
+        if constexpr (WITH_A) dA[k * stride] -= dH * q * sA;
         dT -= fma(dHdT, q, dH * fma(F, qf * dlnkf - qr * dlnkr, q0 * dFdT));
         // d q/d c_b: the reactant and product products with one factor left out
         const double wf = -dH * F * kf, wr = dH * F * kr;
@@ -2033,6 +2033,118 @@ template <int M>
 int run_temperature_at(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T)
 {
     if (n > 0) k_temperature_at<M><<<grid_for(n), LBMK_BLOCK, 0, a.stream>>>(a, n, Y, e, T0, T);
+    return (int)cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------
+// Gradient of J = sum_nodes hdot^c with respect to the stored populations
+// F of the current state (periodic lattices), the source term of the
+// objective in an adjoint of the step.  Node n pulls P_si(n) = F_si(n - c_i)
+// and forms rho_a (a < M-1), rho, j and rho E from the pulled sets; the
+// slaved density is rho - sum_a rho_a, Y_a = rho_a / rho, and T solves
+// sum_a Y_a U_a(T) = e with e = rho E / rho - |j|^2 / (2 rho^2).  By the
+// implicit function theorem dT = (de - sum_a U_a dY_a) / C_v.  With
+// G_T = d hdot/dT and G_a = d hdot/d rho_a (hrr_node) and l = G_T / C_v:
+//   d hdot/d rho_s = G_s - G_{M-1} - l (U_s - U_{M-1}) / rho   (s < M-1)
+//   d hdot/d rho   = G_{M-1} + l (de/drho - (U_{M-1} - sum_a Y_a U_a) / rho),
+//                    de/drho = -rho E / rho^2 + |j|^2 / rho^3
+//   d hdot/d j_d   = -l u_d / rho,      d hdot/d (rho E) = l / rho,
+// and dJ/dF_si(x) is the value of node x + c_i for its set (for f:
+// d/drho + c_i . d/dj).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ double dpoly5(const double u[6], double T)
+{
+    return fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
+}
+
+// adj [M + 4][N]: d hdot/d rho_s (s < M-1), d/d rho, d/d j (3), d/d rho E.
+template <int M>
+__global__ void __launch_bounds__(LBMK_HRR_THREADS, 3) k_hrr_adj(StepArgs a, double *adj)
+{
+    const MechConst &mc = c_mech[a.slot];
+    const int n = blockIdx.x * LBMK_HRR_THREADS + threadIdx.x;
+    if (n >= a.N) return;
+    const size_t N = a.N;
+    Node nd;
+    nd.n = n;
+    node_at(nd, a);
+    PullIdx p;
+    make_pull(p, nd, a);
+    double rho_a[M];
+    Real ja[M][3];
+    Sums sm;
+    pull_moments<M, false>(mc, a, p, n, rho_a, ja, sm);
+    const double rho = sm.rho;
+    double rest = 0.0;
+#pragma unroll
+    for (int s = 0; s < M - 1; ++s) rest += rho_a[s];
+    rho_a[M - 1] = rho - rest;
+    double Y[M];
+#pragma unroll
+    for (int s = 0; s < M; ++s) Y[s] = rho_a[s] / rho;
+    const double u[3] = {sm.j[0] / rho, sm.j[1] / rho, sm.j[2] / rho};
+    const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double eu[6];
+    mixture_energy_poly<M>(mc, Y, eu);
+    const double T = solve_T(eu, sm.rhoE / rho - 0.5 * usq, a.macro[DR_T * N + n], a.status);
+    double GT, G[M];
+    hrr_node<M, false>(mc, T, rho_a, &GT, G, nullptr, 0);
+    const double l = GT / dpoly5(eu, T), ir = 1.0 / rho;
+    double U[M], Umix = 0.0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        U[s] = poly5(mc.uco[s], T);
+        Umix = fma(Y[s], U[s], Umix);
+    }
+#pragma unroll
+    for (int s = 0; s < M - 1; ++s) adj[(size_t)s * N + n] = G[s] - G[M - 1] - l * (U[s] - U[M - 1]) * ir;
+    const double jsq = sm.j[0] * sm.j[0] + sm.j[1] * sm.j[1] + sm.j[2] * sm.j[2];
+    const double dedrho = (jsq * ir - sm.rhoE) * ir * ir;
+    adj[(size_t)(M - 1) * N + n] = G[M - 1] + l * (dedrho - (U[M - 1] - Umix) * ir);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) adj[(size_t)(M + d) * N + n] = -l * u[d] * ir;
+    adj[(size_t)(M + 3) * N + n] = l * ir;
+}
+
+// dJ/dF of set s (0..M), out [27][N]: each direction gathers from x + c_i.
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_hrr_adj_gather(StepArgs a, const double *adj, int s, double *out)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const size_t N = a.N;
+    StencilIdx st;
+    make_stencil(st, nd, a);
+    for_dirs<0, LBMK_Q>([&](auto dd) {
+        constexpr int I = decltype(dd)::value;
+        const size_t nb = nb_of<I>(st, a);
+        double v;
+        if (s < M - 1) {
+            v = adj[(size_t)s * N + nb];
+        } else if (s == M - 1) {
+            v = adj[(size_t)(M - 1) * N + nb];
+            if (CX(I)) v += CX(I) * adj[(size_t)M * N + nb];
+            if (CY(I)) v += CY(I) * adj[(size_t)(M + 1) * N + nb];
+            if (CZ(I)) v += CZ(I) * adj[(size_t)(M + 2) * N + nb];
+        } else {
+            v = adj[(size_t)(M + 3) * N + nb];
+        }
+        out[(size_t)I * N + nd.n] = v;
+    });
+}
+
+template <int M>
+int run_hrr_adj(const StepArgs &a, double *adj)
+{
+    k_hrr_adj<M><<<grid_for(a.N, LBMK_HRR_THREADS), LBMK_HRR_THREADS, 0, a.stream>>>(a, adj);
+    return (int)cudaGetLastError();
+}
+
+template <int M>
+int run_hrr_adj_gather(const StepArgs &a, const double *adj, int s, double *out)
+{
+    k_hrr_adj_gather<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, adj, s, out);
     return (int)cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ _lib.lbm_moments_count.argtypes = [C.c_void_p, C.c_uint]
 _lib.lbm_moments_count.restype = C.c_size_t
 _lib.lbm_get_populations.argtypes = [C.c_void_p, _dp]
 _lib.lbm_heat_release.argtypes = [C.c_void_p, _dp, _dp, C.c_void_p, C.c_void_p]
+_lib.lbm_heat_release_adjoint.argtypes = [C.c_void_p, C.c_void_p]
 _lib.lbm_chemistry_at.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 7
 _lib.lbm_temperature_at.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 4
 _lib.lbm_state_buffer.argtypes = [C.c_void_p]
@@ -101,7 +102,7 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
-            "lbm_chemistry_at", "lbm_temperature_at"]
+            "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint"]
 
 
 def library_path() -> str:
@@ -200,6 +201,11 @@ def lbm_heat_release(ctx, J: np.ndarray, dlogA, dT_ptr, drho_ptr) -> int:
         assert dlogA.dtype == np.float64 and dlogA.flags.c_contiguous
     return _lib.lbm_heat_release(ctx, J.ctypes.data_as(_dp), dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
                                  C.c_void_p(dT_ptr) if dT_ptr else None, C.c_void_p(drho_ptr) if drho_ptr else None)
+
+
+def lbm_heat_release_adjoint(ctx, out_ptr: int) -> int:
+    """out_ptr: host or device address of double [M+1][27][N]."""
+    return _lib.lbm_heat_release_adjoint(ctx, C.c_void_p(out_ptr) if out_ptr else None)
 
 
 def lbm_chemistry_at(ctx, n: int, rho_a_ptr: int, T_ptr: int, rho_dot_ptr=None, hdot_ptr=None, dT_ptr=None,
@@ -458,6 +464,18 @@ class Solver:
             dr = np.empty((self.M, self.N))
             _check(lbm_heat_release(self.ctx, J, dA, dT.ctypes.data, dr.ctypes.data), "lbm_heat_release")
         return float(J[0]), dA, dT, dr
+
+    @_on_device
+    def heat_release_adjoint(self, device: bool = False):
+        """dJ/dF [M+1, 27, N] of J = sum of hdot^c at the current state (see
+        lbm_heat_release_adjoint); numpy, or a torch tensor on the device."""
+        if device:
+            out = self.torch.empty((self.S, 27, self.N), dtype=self.torch.float64, device=self.device)
+            _check(lbm_heat_release_adjoint(self.ctx, out.data_ptr()), "lbm_heat_release_adjoint")
+        else:
+            out = np.empty((self.S, 27, self.N))
+            _check(lbm_heat_release_adjoint(self.ctx, out.ctypes.data), "lbm_heat_release_adjoint")
+        return out
 
     @_on_device
     def chemistry_at(self, rho_a, T):

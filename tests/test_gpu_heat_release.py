@@ -209,3 +209,83 @@ def test_node_functions_argument_checks(lbm):
     g = s.chemistry_at(m["rho_a"], m["T"])
     assert abs(J - g["hdot"].sum()) <= 1e-12 * np.abs(g["hdot"]).sum()
     s.close()
+
+
+def _near_hot(prob, count, seed):
+    rng = np.random.default_rng(seed)
+    hot = np.flatnonzero(prob.init.T > 1000.0)
+    lat = prob.lattice
+    idx = np.arange(lat.n_nodes)
+    x, y, z = idx % lat.nx, (idx // lat.nx) % lat.ny, idx // (lat.nx * lat.ny)
+    cx, cy, cz = lat.nx // 2, lat.ny // 2, lat.nz // 2
+    near = np.flatnonzero((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2 <= 9)
+    return rng.choice(np.union1d(hot, near), count, replace=False)
+
+
+def test_population_gradient_against_oracle(orc, lbm):
+    """dJ/dF (lbm_heat_release_adjoint, double) against central differences
+    of the oracle's J with respect to single populations of its own state
+    after 2 steps: the H2 and O2 sets, the mixture set f and the energy set
+    g, rest and moving directions; 1e-5 of the largest sampled value, 1e-4
+    of each.  The trace H radical's set separately: its populations are
+    ~1e-13 of the density, so its difference step is 1e-2 of them (a step
+    of 1e-6 moves hdot^c by less than its rounding), and its bar 1e-3."""
+    prob = w.sphere3d_problem(shape=(10, 8, 6), radius=2.5)
+    M = prob.species.M
+    o = orc.Oracle.from_problem(prob)
+    assert o.step(2) == 0
+    s = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    s.step(2)
+    G = s.heat_release_adjoint()
+    Gd = s.heat_release_adjoint(device=True).cpu().numpy()
+    s.close()
+    assert np.array_equal(G, Gd)
+    rng = np.random.default_rng(31)
+    nodes = _near_hot(prob, 8, 32)
+    samples = []
+    for k, x in enumerate(nodes):
+        for st in (0, 1, M - 1, M):
+            samples.append((int(x), st, int(rng.integers(27))))
+    one = hrr_fd.oracle_of(orc, prob.species, prob.mech)
+    fd = hrr_fd.d_dpop(o, one, samples)
+    got = np.array([G[st, i, x] for (x, st, i) in samples])
+    scale = np.abs(fd).max()
+    assert scale > 0
+    assert np.abs(got - fd).max() <= 1e-5 * scale
+    big = np.abs(fd) > 1e-3 * scale
+    assert np.all(np.abs(got - fd)[big] <= 1e-4 * np.abs(fd)[big])
+    radical = [(int(x), 3, int(rng.integers(27))) for x in nodes]
+    fd_r = hrr_fd.d_dpop(o, one, radical, rel=1e-2)
+    got_r = np.array([G[st, i, x] for (x, st, i) in radical])
+    assert np.abs(fd_r).max() > 0
+    assert np.all(np.abs(got_r - fd_r) <= 1e-3 * np.abs(fd_r) + 1e-5 * scale)
+
+
+def test_population_gradient_is_the_directional_derivative(lbm):
+    """<dJ/dF, delta> equals (J(F + eps delta) - J(F - eps delta)) / (2 eps)
+    with J from lbm_heat_release, perturbing the double state in place
+    (48 x 40 x 36 nodes, a seeded relative perturbation of every
+    population): 1e-6."""
+    import torch
+    prob = w.sphere3d_problem(shape=(48, 40, 36), radius=8.0)
+    s = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    s.step(3)
+    G = s.heat_release_adjoint(device=True)
+    n_pop = s.S * 27 * s.N
+    ptr = lbm.lbm_state_buffer(s.ctx)
+    buf = s.pop[0] if s.pop[0].data_ptr() == ptr else s.pop[1]
+    F = buf.view(torch.float64)[:n_pop].view(s.S, 27, s.N)
+    gen = torch.Generator(device=G.device).manual_seed(41)
+    delta = F * (2 * torch.rand(F.shape, generator=gen, device=G.device, dtype=torch.float64) - 1)
+    eps = 1e-6
+    F0 = F.clone()
+    F.add_(eps * delta)
+    Jp = s.heat_release(gradients=False)
+    F.copy_(F0)
+    F.sub_(eps * delta)
+    Jm = s.heat_release(gradients=False)
+    F.copy_(F0)
+    fd = (Jp - Jm) / (2 * eps)
+    ad = float((G * delta).sum().item())
+    s.close()
+    assert ad != 0.0 and abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
