@@ -32,17 +32,44 @@ class OrcParams(C.Structure):
     ]
 
 
+def _compile(src: Path, out: Path) -> None:
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
+           str(src), "-o", str(out), "-lm"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (-O2, no fast-math, OpenMP over nodes)."""
     BUILD.mkdir(exist_ok=True)
     if LIB.exists() and not force and LIB.stat().st_mtime >= SRC.stat().st_mtime:
         return LIB
     tmp = BUILD / f"liblbm_oracle.{os.getpid()}.so"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-fno-fast-math",
-           str(SRC), "-o", str(tmp), "-lm"]
-    subprocess.run(cmd, check=True)
+    _compile(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
+
+
+def _bind(L):
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(OrcParams)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_init.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double]
+    L.orc_step.argtypes = [C.c_void_p, C.c_int]
+    L.orc_moments.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp]
+    L.orc_get_pop.argtypes = [C.c_void_p, _dp]
+    L.orc_set_pop.argtypes = [C.c_void_p, _dp]
+    L.orc_get_T.argtypes = [C.c_void_p, _dp]
+    L.orc_set_T.argtypes = [C.c_void_p, _dp]
+    L.orc_thermo.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp, _dp]
+    L.orc_temperature.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
+    L.orc_rates.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
+    L.orc_heat_release.restype = C.c_double
+    L.orc_heat_release.argtypes = [C.c_void_p, _dp, C.c_double]
+    L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
+    L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
+    L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
+    L.orc_grad_pop.argtypes = [C.c_double, _dp, _dp, _dp]
+    return L
 
 
 _lib = None
@@ -51,28 +78,20 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(str(build()))
-        L = _lib
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(OrcParams)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_init.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_double]
-        L.orc_step.argtypes = [C.c_void_p, C.c_int]
-        L.orc_moments.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, _dp]
-        L.orc_get_pop.argtypes = [C.c_void_p, _dp]
-        L.orc_set_pop.argtypes = [C.c_void_p, _dp]
-        L.orc_get_T.argtypes = [C.c_void_p, _dp]
-        L.orc_set_T.argtypes = [C.c_void_p, _dp]
-        L.orc_thermo.argtypes = [C.c_void_p, C.c_double, _dp, _dp, _dp, _dp]
-        L.orc_temperature.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
-        L.orc_rates.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
-        L.orc_heat_release.restype = C.c_double
-        L.orc_heat_release.argtypes = [C.c_void_p, _dp, C.c_double]
-        L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
-        L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
-        L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
-        L.orc_grad_pop.argtypes = [C.c_double, _dp, _dp, _dp]
+        _lib = _bind(C.CDLL(str(build())))
     return _lib
+
+
+def load_variant(source_text: str, workdir) -> C.CDLL:
+    """Compiles a modified copy of the oracle source (a test plants a
+    mistake in it to show that a pin catches it) and returns its bound
+    library, for Oracle(..., library=...)."""
+    workdir = Path(workdir)
+    src = workdir / "lbm_oracle_variant.c"
+    out = workdir / "liblbm_oracle_variant.so"
+    src.write_text(source_text)
+    _compile(src, out)
+    return _bind(C.CDLL(str(out)))
 
 
 def _d(a):
@@ -86,8 +105,9 @@ def _i(a):
 class Oracle:
     """One oracle instance bound to a workload.Problem (or its parts)."""
 
-    def __init__(self, lattice, species, mech):
+    def __init__(self, lattice, species, mech, library=None):
         self.lattice, self.species, self.mech = lattice, species, mech
+        self._L = library if library is not None else lib()
         self.M = species.M
         self.S = self.M + 1
         self.N = lattice.nx * lattice.ny * lattice.nz
@@ -111,13 +131,13 @@ class Oracle:
             log_A=d("log_A", mech.log_A), b=d("b", mech.b), theta=d("theta", mech.theta),
             rtype=i("rtype", mech.rtype), eff=d("eff", mech.eff), low=d("low", mech.low),
             reversible=i("reversible", mech.reversible), T_ref=mech.T_ref, P0=mech.P0)
-        self._h = lib().orc_create(C.byref(p))
+        self._h = self._L.orc_create(C.byref(p))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
 
     @classmethod
-    def from_problem(cls, prob, init: bool = True):
-        o = cls(prob.lattice, prob.species, prob.mech)
+    def from_problem(cls, prob, init: bool = True, library=None):
+        o = cls(prob.lattice, prob.species, prob.mech, library=library)
         if init:
             o.init(prob.init.X, prob.init.T, prob.init.u, prob.init.P)
         return o
@@ -125,23 +145,23 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     def init(self, X, T, u, P):
         X = np.ascontiguousarray(X, dtype=np.float64)
         T = np.ascontiguousarray(T, dtype=np.float64)
         u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
-        return lib().orc_init(self._h, _d(X), _d(T), _d(u), float(P))
+        return self._L.orc_init(self._h, _d(X), _d(T), _d(u), float(P))
 
     def step(self, n: int = 1) -> int:
-        return lib().orc_step(self._h, int(n))
+        return self._L.orc_step(self._h, int(n))
 
     def moments(self):
         M, N = self.M, self.N
         out = dict(rho_a=np.empty((M, N)), rhou=np.empty((3, N)), rhoE=np.empty(N),
                    T=np.empty(N), j_a=np.empty((M, 3, N)))
-        st = lib().orc_moments(self._h, _d(out["rho_a"]), _d(out["rhou"]), _d(out["rhoE"]),
+        st = self._L.orc_moments(self._h, _d(out["rho_a"]), _d(out["rhou"]), _d(out["rhoE"]),
                                _d(out["T"]), _d(out["j_a"]))
         out["status"] = st
         rho = out["rho_a"].sum(axis=0)
@@ -151,59 +171,59 @@ class Oracle:
 
     def get_pop(self):
         a = np.empty((self.N, self.S, 27))
-        lib().orc_get_pop(self._h, _d(a))
+        self._L.orc_get_pop(self._h, _d(a))
         return a
 
     def set_pop(self, a):
         a = np.ascontiguousarray(a, dtype=np.float64)
         assert a.shape == (self.N, self.S, 27)
-        lib().orc_set_pop(self._h, _d(a))
+        self._L.orc_set_pop(self._h, _d(a))
 
     def get_T(self):
         a = np.empty(self.N)
-        lib().orc_get_T(self._h, _d(a))
+        self._L.orc_get_T(self._h, _d(a))
         return a
 
     def set_T(self, a):
         a = np.ascontiguousarray(a, dtype=np.float64)
-        lib().orc_set_T(self._h, _d(a))
+        self._L.orc_set_T(self._h, _d(a))
 
     # point-wise pieces -------------------------------------------------
     def thermo(self, T):
         M = self.M
         U, H, Cv, g = (np.empty(M) for _ in range(4))
-        lib().orc_thermo(self._h, float(T), _d(U), _d(H), _d(Cv), _d(g))
+        self._L.orc_thermo(self._h, float(T), _d(U), _d(H), _d(Cv), _d(g))
         return dict(U=U, H=H, Cv=Cv, gRT=g)
 
     def temperature(self, Y, e, T_guess):
         Y = np.ascontiguousarray(Y, dtype=np.float64)
         T = np.zeros(1)
-        st = lib().orc_temperature(self._h, _d(Y), float(e), float(T_guess), _d(T))
+        st = self._L.orc_temperature(self._h, _d(Y), float(e), float(T_guess), _d(T))
         return float(T[0]), st
 
     def rates(self, rho_a, T):
         rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
         w = np.empty(self.M)
-        lib().orc_rates(self._h, _d(rho_a), float(T), _d(w))
+        self._L.orc_rates(self._h, _d(rho_a), float(T), _d(w))
         return w
 
     def heat_release(self, rho_a, T):
         """hdot^c = -sum_a H_a rho_dot_a at one node state (Sec. 5b)."""
         rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
-        return float(lib().orc_heat_release(self._h, _d(rho_a), float(T)))
+        return float(self._L.orc_heat_release(self._h, _d(rho_a), float(T)))
 
     def diffusion_velocities(self, Y, ua_minus_u, T):
         Y = np.ascontiguousarray(Y, dtype=np.float64)
         r = np.ascontiguousarray(ua_minus_u, dtype=np.float64).reshape(self.M, 3)
         du = np.empty((self.M, 3))
-        st = lib().orc_diffusion_velocities(self._h, _d(Y), _d(r), float(T), _d(du))
+        st = self._L.orc_diffusion_velocities(self._h, _d(Y), _d(r), float(T), _d(du))
         return du, st
 
     def equilibrium_sets(self, rho_a, u, T):
         rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty((self.S, 27))
-        lib().orc_equilibrium_sets(self._h, _d(rho_a), _d(u), float(T), _d(out))
+        self._L.orc_equilibrium_sets(self._h, _d(rho_a), _d(u), float(T), _d(out))
         return out
 
 

@@ -33,7 +33,7 @@
  *   slaving of the last species ...................... Eq. (strongest)
  *   heat release rate hdot^c ......................... Sec. 5b (circular flame)
  *
- * Readings where the paper is silent (all recorded in the design notes):
+ * Readings where the paper is silent:
  *   - lattice gradients: d_alpha phi(x) = (1/theta) sum_i w_i c_ia phi(x+c_i),
  *     theta = 1/3, applied twice for X (inner derivative, multiply by
  *     (1/omega - 1/2), outer derivative);

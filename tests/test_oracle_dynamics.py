@@ -282,3 +282,92 @@ def test_sound_attenuation_bulk_viscosity(orc):
     r256 = _sound_attenuation_ratio(orc, 256, 7680)
     assert abs(r256 - 1) < 0.02, r256
     assert abs(r128 - 1) / abs(r256 - 1) > 3.0, (r128, r256)
+
+
+# ---------------------------------------------------------------------------
+# Interdiffusion heat flux (Eqs. (qdiff), (corrFourier), (qneq), (dtE))
+# ---------------------------------------------------------------------------
+def _binary_unequal_enthalpy(nx, dh=10.0, cp_R=(2.5, 4.5), D=0.02, r_lat=0.4, W0=20.0):
+    """Two species of equal molar mass (equal R_a, no barodiffusion) whose
+    enthalpies differ: different heat capacities and a formation enthalpy
+    difference of dh R T0 (Eq. (specHa))."""
+    sp, mech, lat = _binary_equal_mass(nx, D=D, r_lat=r_lat, W0=W0)
+    R = r_lat / W0
+    sp.cp_R = np.array(cp_R, dtype=float)
+    sp.h_form = np.array([0.0, -dh * R * sp.T0])
+    return sp, mech, lat
+
+
+def _interdiffusion_run(nx, library=None, dY=0.02, dh=10.0, D=0.02):
+    """Y_1 = 1/2 + dY sin(k x) at rest, uniform T = T0 and P.  Returns the
+    largest temperature-mode amplitude over the first 1/(D k^2) steps in
+    units of (Delta H / C_v) dY, and the decay rate of the Y mode over D k^2.
+
+    With q = -lambda grad T + rho sum_a H_a Y_a V_a (Eq. (qneq)) the energy
+    equation at rest, uniform T and P reduces to
+        rho C_v dT/dt = -sum_a R_a T div(rho_a V_a) = -R T div(sum_a rho_a V_a) = 0
+    for equal R_a, so T stays uniform to leading order in k.  A wrong
+    q^diff or q^corr leaves a flux ~ Delta H rho D grad Y_1 in the energy
+    equation and drives a T mode of order (Delta H / C_v) dY."""
+    import oracle
+    sp, mech, lat = _binary_unequal_enthalpy(nx, dh=dh, D=D)
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    X1 = 0.5 + dY * np.sin(k * x)
+    o = oracle.Oracle(lat, sp, mech, library=library)
+    o.init(np.stack([X1, 1 - X1]), np.ones(nx), None, sp.r_lat / sp.W[0])
+    R = sp.r_lat / sp.W[0]
+    Cv = 0.5 * (sp.cp_R[0] - 1 + sp.cp_R[1] - 1) * R
+    scale = dh * R / Cv * dY
+    steps = int(round(1.0 / (D * k * k)))
+    chunk = max(1, steps // 40)
+    t, tmax, ys = 0, 0.0, []
+    while True:
+        m = o.moments()
+        assert m["status"] == 0
+        tmax = max(tmax, _mode_amplitude(m["T"], nx))
+        ys.append((t, _mode_amplitude(m["Y"][0], nx)))
+        if t >= steps:
+            break
+        assert o.step(chunk) == 0
+        t += chunk
+    (t0, a0), (t1, a1) = ys[len(ys) // 4], ys[-1]
+    rate = math.log(a0 / a1) / (t1 - t0)
+    return tmax / scale, rate / (D * k * k)
+
+
+def test_interdiffusion_heat_flux_keeps_temperature_uniform(orc):
+    """Binary mixture of equal molar masses but unequal enthalpies: Y decays
+    at D_12 k^2 (Eq. (constit2)) while T stays uniform; the residual
+    temperature mode is below 1 % of (Delta H / C_v) dY and falls as k^2.
+    Every other hydrodynamic pin uses species of equal enthalpy, for which
+    q^diff and q^corr vanish identically."""
+    r32, d32 = _interdiffusion_run(32)
+    r64, d64 = _interdiffusion_run(64)
+    assert r32 < 0.01 and r64 < 0.004, (r32, r64)
+    assert r32 / r64 > 3.0, (r32, r64)                 # second order in k
+    assert abs(d64 - 1) < 0.02, (d32, d64)              # Fick decay D_12 k^2 ...
+    assert abs(d32 - 1) / abs(d64 - 1) > 3.0, (d32, d64)  # ... reached at second order
+
+
+_QDIFF = "double qdiff = (omega1 / (omega - omega1)) * rho * sumHYdu[b];"
+_QCORR = "double qcorr = 0.5 * ((omega1 - 2.0) / (omega1 - omega)) * P * sumHgradY[b];"
+_GRADY = "s->gradY[(n * M + a) * 3 + d] = gY[a][d] / THETA;"
+
+
+@pytest.mark.parametrize("mutant,old,new", [
+    ("q^diff dropped", _QDIFF, "double qdiff = 0.0;"),
+    ("q^corr prefactor sign flipped", _QCORR, _QCORR.replace("0.5 *", "-0.5 *")),
+    ("q^corr half dropped", _QCORR, _QCORR.replace("0.5 * ", "")),
+    ("grad Y sign flipped", _GRADY, _GRADY.replace("gY[a][d] / THETA", "-gY[a][d] / THETA")),
+])
+def test_interdiffusion_pin_catches_planted_mistakes(orc, tmp_path, mutant, old, new):
+    """The pin above fails for an oracle with a plausible mistake planted in
+    q^diff (Eq. (qdiff)), q^corr (Eq. (corrFourier)) or the lattice
+    gradient of Y that feeds it: the temperature mode then reaches 20-60 %
+    of (Delta H / C_v) dY, against 0.75 % for the oracle as written."""
+    src = orc.SRC.read_text()
+    assert src.count(old) == 1, mutant
+    lib = orc.load_variant(src.replace(old, new), tmp_path)
+    r32, _ = _interdiffusion_run(32, library=lib)
+    assert r32 > 0.1, (mutant, r32)
