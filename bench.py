@@ -30,10 +30,12 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MLUPS (M+2 pop sets + chemistry), mixed vs FP64 step, % of HBM roofline"
 FALLBACK_HBM_GBS = 6800.0
 
-# FP64 arithmetic peak of the GPU: 152 SMs x 2 FP64 FMA per SM and clock
-# x 2 flops x 2070 MHz (maximum SM clock).
+# FP64 arithmetic peak derived from the unit counts: 152 SMs x 2 FP64 FMA
+# per SM and clock x 2 flops x 2070 MHz (maximum SM clock).  The roofline
+# uses the peak measured by lbm_fp64_probe on the same GPU in the same run;
+# the derived figure is reported beside it.
 SM_COUNT, FP64_FMA_PER_SM_CLK, SM_MAX_MHZ = 152, 2, 2070.0
-FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_TFLOPS_DERIVED = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 # Per lattice node and launch, counted by ncu on the 128^3 instance of this
 # workload for the kernels as they stand (profiles/ has the captures):
@@ -64,6 +66,39 @@ def launches_per_step(ghost: bool) -> int:
     collisions (the production rates are formed inside the species
     collision), plus the ghost-node kernel for non-periodic x."""
     return 4 + (1 if ghost else 0)
+
+
+def algorithmic_bytes_per_node(M: int, mixed: bool) -> int:
+    """One read and one write of the (M+1) stored sets of 27 populations,
+    4 bytes each in mixed precision and 8 in double: 2160 and 4320 B at
+    M = 9.  The mixed layout moves a little more (stored_bytes_per_node:
+    double rest populations and a double energy set)."""
+    return 2 * (M + 1) * 27 * (4 if mixed else 8)
+
+
+def fp64_probe(lbm, torch, stream, blocks_per_sm: int = 8):
+    """Measured double-precision throughput of this GPU (lbm_fp64_probe):
+    fused multiply-add in TFLOP/s, CUDA's exp and log in G calls/s, each a
+    single launch of 152 x blocks_per_sm blocks of 256 threads timed with
+    CUDA events after a short warm-up launch."""
+    blocks = SM_COUNT * blocks_per_sm
+    sink = torch.zeros(blocks, dtype=torch.float64, device=stream.device)
+    out = {}
+    for name, kind, iters in (("dfma", lbm.LBM_PROBE_DFMA, 24000), ("exp", lbm.LBM_PROBE_EXP, 3000),
+                              ("log", lbm.LBM_PROBE_LOG, 3000)):
+        st, _, _ = lbm.lbm_fp64_probe(kind, blocks, max(1, iters // 50), sink.data_ptr(), stream.cuda_stream)
+        if st != lbm.LBM_OK:
+            raise lbm.LBMError(st, "lbm_fp64_probe")
+        st, ms, rate = lbm.lbm_fp64_probe(kind, blocks, iters, sink.data_ptr(), stream.cuda_stream)
+        if st != lbm.LBM_OK:
+            raise lbm.LBMError(st, "lbm_fp64_probe")
+        out[name] = {"ms": ms, "rate": rate}
+    return {"dfma_tflops": out["dfma"]["rate"] / 1e12, "exp_gcalls": out["exp"]["rate"] / 1e9,
+            "log_gcalls": out["log"]["rate"] / 1e9,
+            "ms": {k: v["ms"] for k, v in out.items()},
+            "derived_tflops": FP64_PEAK_TFLOPS_DERIVED,
+            "how": f"lbm_fp64_probe: {blocks} blocks x 256 threads; 8 independent FMA chains per thread "
+                   f"(2 flop each), 4 independent exp / log chains per thread; CUDA events"}
 
 
 def stored_bytes_per_node(M: int, mixed: bool) -> int:
@@ -173,6 +208,57 @@ def _cpu_oracle_single_thread(min_seconds: float = 3.0):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def _cpu_leg(prob, steps: int, warmup: int = 1):
+    """The FP64 oracle stepping one whole workload on all host cores."""
+    import oracle
+    o = oracle.Oracle.from_problem(prob)
+    o.step(warmup)
+    t0 = time.perf_counter()
+    assert o.step(steps) == 0
+    dt = time.perf_counter() - t0
+    N = prob.lattice.n_nodes
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": N * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "seconds": dt, "steps": steps,
+            "nodes": N, "workload": prob.name}
+
+
+def _host_memory_bytes():
+    """Memory this process may still use: MemAvailable, capped by a cgroup limit."""
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    for f in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            v = open(f).read().strip()
+            if v.isdigit():
+                avail = min(avail or int(v), int(v))
+        except OSError:
+            pass
+    return avail
+
+
+def run_cpu_legs(args):
+    """The oracle's three timed legs: the three-gas 64x4x4 workload for 200
+    steps, the 32^3 expanding flame for 1000 steps, and 10 steps of the
+    256^3 benchmark lattice (only when the host has memory for the oracle's
+    ~5.1 kB per node, with half again to spare)."""
+    import workload as w
+    legs = {"config1_64x4x4_M3_200": _cpu_leg(w.config1_problem(), 200),
+            "sphere3d_32^3_M9_1000": _cpu_leg(w.sphere3d_problem(n=32, radius=8.0), 1000)}
+    need = 256 ** 3 * 5200
+    have = _host_memory_bytes()
+    if have is not None and have > 1.5 * need:
+        legs["sphere3d_256^3_M9_10"] = _cpu_leg(w.sphere3d_problem(n=256, radius=20.0), 10)
+    else:
+        legs["sphere3d_256^3_M9_10"] = {"skipped": f"needs ~{need / 1e9:.0f} GB of host memory, "
+                                                   f"{(have or 0) / 1e9:.0f} GB available"}
+    print(json.dumps({"metric": "FP64 CPU oracle MLUPS per leg", "legs": legs}), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -247,6 +333,10 @@ def run_ours(args):
     # The timed region: K steps enqueued back to back on the library's
     # stream with CUDA events between the kernels (one wait at the end);
     # the events give the whole-run time and each kernel's launch times.
+    with ClockSampler(local) as clk_probe:
+        probe = fp64_probe(lbm, torch, stream)                     # the FP64 peak, before the timed region
+    probe["clocks"] = clk_probe.summary()
+    FP64_PEAK = probe["dfma_tflops"]
     s = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
     blocks = None if args.skip_autotune else s.autotune(trials=3)   # launch shapes, outside the timed region
     s.step(args.warmup)
@@ -268,7 +358,8 @@ def run_ours(args):
     # of the stored state per node.
     peak, peak_kind = _peaks()
     mixed = precision != lbm.LBM_FP64
-    alg_bytes_node = 2 * stored_bytes_per_node(M, mixed)
+    alg_bytes_node = algorithmic_bytes_per_node(M, mixed)
+    layout_bytes_node = 2 * stored_bytes_per_node(M, mixed)
     step_frac = alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak
     kern_ms = {"k_pre": phases[1], "k_chem": phases[2], "k_grad": phases[3], "k_step_g": phases[4],
                "k_step": phases[5]}
@@ -280,20 +371,24 @@ def run_ours(args):
         e = {"ms": t}
         if flops.get(k):
             e["fp64_tflops"] = flops[k] * N / (t * 1e-3) / 1e12
-            e["fp64_frac"] = e["fp64_tflops"] / FP64_PEAK_TFLOPS
+            e["fp64_frac"] = e["fp64_tflops"] / FP64_PEAK
         if dram.get(k):
             e["dram_gbs"] = dram[k] * N / (t * 1e-3) / 1e9
         kernels[k] = e
     dom = max((k for k in ("k_pre", "k_chem", "k_step_g", "k_step") if k in kern_ms), key=lambda k: kern_ms[k])
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom].get("fp64_tflops"),
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": kernels[dom].get("fp64_frac"),
+                "peak": FP64_PEAK, "unit": "TFLOP/s", "frac": kernels[dom].get("fp64_frac"),
                 "traffic": dram[dom] * N if dram.get(dom) else None,
                 "flops_per_node": flops.get(dom),
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"}
+                "peak_source": "measured: lbm_fp64_probe DFMA throughput in this run (of measured)",
+                "frac_of_derived_peak": (kernels[dom]["fp64_tflops"] / FP64_PEAK_TFLOPS_DERIVED
+                                         if kernels[dom].get("fp64_tflops") else None)}
     roofline_hbm = {"bound": "hbm", "kernel": "whole step",
                     "achieved": alg_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9, "peak": peak,
                     "unit": "GB/s", "frac": step_frac, "algorithmic_bytes_per_node": alg_bytes_node,
-                    "peak_source": peak_kind}
+                    "layout_bytes_per_node": layout_bytes_node,
+                    "layout_frac": layout_bytes_node * N / (ms * 1e-3 / args.steps) / 1e9 / peak,
+                    "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
     # ---- heat-release objective and its sensitivities ---------------------
     # lbm_heat_release on the state the timed steps left: hdot^c summed over
@@ -326,7 +421,7 @@ def run_ours(args):
         f_h = HRR_FLOPS_PER_NODE.get(args.precision)
         if f_h:
             hrr["fp64_tflops"] = f_h * N / (t_hrr * 1e-3) / 1e12
-            hrr["fp64_frac"] = hrr["fp64_tflops"] / FP64_PEAK_TFLOPS
+            hrr["fp64_frac"] = hrr["fp64_tflops"] / FP64_PEAK
             hrr["flops_per_node"] = f_h
         del dT, dr
         torch.cuda.empty_cache()
@@ -387,7 +482,7 @@ def run_ours(args):
         k64 = max(2, args.steps // 2)
         ms64 = timed_steps(s64, k64)
         fp64 = {"mlups": N * k64 * world / (ms64 * 1e-3) / 1e6, "steps": k64,
-                "hbm_frac": 2 * stored_bytes_per_node(M, False) * N / (ms64 * 1e-3 / k64) / 1e9 / peak}
+                "hbm_frac": algorithmic_bytes_per_node(M, False) * N / (ms64 * 1e-3 / k64) / 1e9 / peak}
         s64.close()
         del s64
         torch.cuda.empty_cache()
@@ -398,6 +493,7 @@ def run_ours(args):
         one = _cpu_oracle_single_thread()
         if one:
             cpu["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+        cpu["legs"] = {"config1_64x4x4_M3_200": _cpu_leg(w.config1_problem(), 200)}
 
     if rank == 0:
         line = {
@@ -415,6 +511,7 @@ def run_ours(args):
                          "gradients": phases[3], "energy_collision": phases[4], "species_collision": phases[5]},
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
+            "fp64_peak_measured": probe,
             "kernels": kernels,
             "autotuned_blocks": blocks,
             "mixed_fast_step": fast,
@@ -587,6 +684,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-hrr", action="store_true", help="skip the heat-release sensitivity measurement")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
+    ap.add_argument("--cpu-legs", action="store_true",
+                    help="instead of timing the GPU: the oracle's timed legs (64x4x4 200 steps, 32^3 1000 steps, "
+                         "256^3 10 steps)")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="instead of timing: field error of the mixed modes against double after this many steps")
     args = ap.parse_args()
@@ -594,6 +694,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.cpu_legs:
+        run_cpu_legs(args)
     elif args.accuracy_steps > 0:
         run_accuracy(args)
     elif args.workload == "flames48":

@@ -345,16 +345,15 @@ int lbm_set_references(lbm_ctx *ctx, const float *ref);
 /* One double-precision time step that allocates nothing (the paper has no
  * counterpart; this is a service for callers).  Some callers cannot call
  * cudaMalloc where they need to step the lattice: a plugin or callback
- * running inside another framework that owns every device allocation, a
- * process whose device allocator is capped or exhausted, or code that must
- * avoid the implicit synchronisation an allocation can cause.  They can
- * still pass their own population buffers, so this entry point takes
+ * running inside another framework that owns every device allocation, or
+ * a process whose device allocator is capped or exhausted.  They can still
+ * pass their own population buffers, so this entry point takes
  *   pop_in   device, double [M+1][27][N]: post-collision state (input)
  *   pop_out  device, double [M+1][27][N]: the state one step later (output,
  *            distinct from pop_in)
  *   T_io     device, double [N]: starting temperatures for the Newton
  *            iteration on input; the temperatures of the step's moments on
- *            output
+ *            output (must not overlap either population buffer)
  * and keeps the per-node macroscopic record, the x-face ghost planes and the
  * status word in a fixed device array of LBM_FIXED_SCRATCH_BYTES compiled
  * into the library, which every GPU that loads the library holds until the
@@ -363,14 +362,15 @@ int lbm_set_references(lbm_ctx *ctx, const float *ref);
  * Limits: precision LBM_FP64 only (else LBM_ERR_UNSUPPORTED); the lattice
  * must fit, 256 + (31 + 8M) N 8 bytes plus, for non-periodic x,
  * 2 (M+1) 27 ny nz 8 bytes <= LBM_FIXED_SCRATCH_BYTES (up to 43^3 nodes
- * with M = 9, 53^3 with M = 3), else LBM_ERR_ARG.  The first call on a
+ * with M = 9, 53^3 with M = 3), else LBM_ERR_ARG; pop_in, pop_out and
+ * T_io must not overlap one another (LBM_ERR_ARG).  The first call on a
  * device looks up the array's device
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call uses the same array and it keeps the previous call's
  * contents (the call clears its status word itself), so calls that overlap
  * on the GPU -- on different streams or host threads -- race and must be
- * serialised by the caller.  Waits for the stream and returns like
- * lbm_step. */
+ * serialised by the caller.  Every call waits for the stream (it reads
+ * the status word back) and returns like lbm_step. */
 #define LBM_FIXED_SCRATCH_BYTES (64u << 20)
 int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
                            const double *pop_in, double *pop_out, double *T_io, void *cuda_stream);
@@ -382,6 +382,23 @@ int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const 
  * y_ref, for n arguments x.  x, y, y_ref: device, double [n].  Waits for
  * the stream; LBM_ERR_ARG for NULL pointers or n < 0. */
 int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream);
+
+/* Diagnostic (the paper has no counterpart): throughput of the GPU's
+ * double-precision arithmetic, the peak the step's FP64-bound kernels are
+ * measured against.  kind: LBM_PROBE_DFMA (independent fused multiply-add
+ * chains; rate in flops/s, 2 per FMA), LBM_PROBE_EXP or LBM_PROBE_LOG
+ * (independent chains of CUDA's double exp or log; rate in calls/s).
+ * blocks: grid size (256 threads each; a multiple of the SM count fills the
+ * GPU evenly); iters: loop trips per thread (32 FMA or 4 calls each).
+ * sink: device, double [blocks], never written in practice (it keeps the
+ * compiler from removing the chains).  out: host, double [2]: elapsed
+ * milliseconds (CUDA events on the stream) and the rate.  Waits for the
+ * stream; LBM_ERR_ARG for a bad kind, NULL or host pointers, or
+ * non-positive sizes. */
+#define LBM_PROBE_DFMA 0
+#define LBM_PROBE_EXP 1
+#define LBM_PROBE_LOG 2
+int lbm_fp64_probe(int kind, int blocks, int iters, double *sink, double *out, void *cuda_stream);
 
 /* Frees host state and the status word; never the caller's buffers. */
 int lbm_destroy(lbm_ctx *ctx);

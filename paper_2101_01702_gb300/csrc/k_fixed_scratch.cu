@@ -3,9 +3,8 @@
 //
 // Who needs this: code that runs where cudaMalloc is not available or not
 // allowed at the point of the call -- for example a host callback or a
-// plugin inside another framework that owns every device allocation, a
-// process whose allocator is capped or already exhausted, or a caller that
-// must not trigger an implicit device synchronisation.  Such callers can
+// plugin inside another framework that owns every device allocation, or a
+// process whose allocator is capped or already exhausted.  Such callers can
 // pass their own population buffers (inputs and outputs) but cannot hand the
 // library the per-node macroscopic record and ghost planes that lbm_step keeps
 // in caller-provided scratch buffers.  Here that scratch lives in
@@ -17,6 +16,7 @@
 // of the tables, so it never touches the contexts created by lbm_create.
 #define LBMK_MIXED 0
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <mutex>
@@ -53,6 +53,12 @@ int scratch_address(void **out)
     return LBM_OK;
 }
 
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
 }  // namespace
 
 extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanism *mech,
@@ -70,6 +76,14 @@ extern "C" int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species 
     const size_t ghost_bytes = lat->bc_x == LBM_BC_PERIODIC ? 0 : 2 * S * LBMK_Q * (size_t)lat->ny * lat->nz * sizeof(double);
     if (N > (size_t)0x7fffffff || 256 + macro_bytes + ghost_bytes > (size_t)LBM_FIXED_SCRATCH_BYTES)
         return LBM_ERR_ARG;     // lattice too large for the fixed scratch array
+    // T_io is copied into the array before the step and back after it, and
+    // pop_out is written while pop_in is read: overlapping ranges would
+    // corrupt the state silently, so they are rejected.
+    const size_t pop_bytes = S * LBMK_Q * N * sizeof(double);
+    if (ranges_overlap(pop_in, pop_bytes, pop_out, pop_bytes) ||
+        ranges_overlap(T_io, N * sizeof(double), pop_in, pop_bytes) ||
+        ranges_overlap(T_io, N * sizeof(double), pop_out, pop_bytes))
+        return LBM_ERR_ARG;
     MechConst mc;
     int st = lbm_pack_tables(sp, mech, mc);
     if (st != LBM_OK) return st;

@@ -102,7 +102,7 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
-            "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint"]
+            "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe"]
 
 
 def library_path() -> str:
@@ -240,6 +240,19 @@ def lbm_exp_check(x_ptr: int, y_ptr: int, y_ref_ptr: int, n: int, stream: int) -
     """The kernels' exponential into y and CUDA's exp into y_ref (device)."""
     return _lib.lbm_exp_check(C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(y_ref_ptr), int(n),
                               C.c_void_p(stream))
+
+
+_lib.lbm_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, _dp, C.c_void_p]
+_lib.lbm_fp64_probe.restype = C.c_int
+LBM_PROBE_DFMA, LBM_PROBE_EXP, LBM_PROBE_LOG = 0, 1, 2
+
+
+def lbm_fp64_probe(kind: int, blocks: int, iters: int, sink_ptr: int, stream: int):
+    """(status, milliseconds, rate) of one probe launch (see include/lbm.h)."""
+    out = np.zeros(2)
+    st = _lib.lbm_fp64_probe(int(kind), int(blocks), int(iters), C.c_void_p(sink_ptr),
+                             out.ctypes.data_as(_dp), C.c_void_p(stream))
+    return st, float(out[0]), float(out[1])
 
 
 def lbm_step_fixed_scratch(lat, sp, mech, pop_in_ptr: int, pop_out_ptr: int, T_io_ptr: int, stream: int) -> int:

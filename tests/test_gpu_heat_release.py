@@ -289,3 +289,29 @@ def test_population_gradient_is_the_directional_derivative(lbm):
     ad = float((G * delta).sum().item())
     s.close()
     assert ad != 0.0 and abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
+def test_population_gradient_mixed_units_match_double(lbm, precision):
+    """lbm_heat_release_adjoint in the mixed units (float deviations plus
+    double rest and energy populations, summed by their own moment pass)
+    against the double unit on the same initial state after 2 steps
+    (10 x 8 x 6): per set, 1e-5 of that set's largest |dJ/dF| -- float
+    storage moves the state by ~1e-7 relative, and the gradient is smooth
+    in the state; the fast unit's float exponential adds ~2e-7."""
+    prob = w.sphere3d_problem(shape=(10, 8, 6), radius=2.5)
+    ref = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    ref.step(2)
+    G_ref = ref.heat_release_adjoint()
+    ref.close()
+    p = {"mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST}[precision]
+    s = lbm.Solver.from_problem(prob, precision=p)
+    s.step(2)
+    G = s.heat_release_adjoint()
+    s.close()
+    assert G.shape == G_ref.shape
+    for st in range(G.shape[0]):
+        scale = np.abs(G_ref[st]).max()
+        assert scale > 0, st
+        err = np.abs(G[st] - G_ref[st]).max() / scale
+        assert err <= 1e-5, (precision, st, err)

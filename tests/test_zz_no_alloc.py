@@ -1,8 +1,8 @@
 """The allocation-free step, lbm_step_fixed_scratch, against lbm_step.
 
 Callers that cannot allocate device memory (a plugin inside a framework
-that owns all allocations, a capped or exhausted allocator, code that must
-not synchronise on an allocation) step the lattice through
+that owns all allocations, a capped or exhausted allocator) step the
+lattice through
 lbm_step_fixed_scratch, which keeps its macroscopic record, ghost planes and
 status word in a device array compiled into the library.  This test calls
 it through the C ABI twice in a row and compares each output -- populations
@@ -78,7 +78,34 @@ def test_fixed_scratch_rejects_lattices_beyond_the_array(lbm):
     ref = lbm.Solver(prob.lattice, prob.species, prob.mech, precision=lbm.LBM_FP64)
     dummy = torch.empty(16, dtype=torch.float64, device="cuda")
     dummy2 = torch.empty(16, dtype=torch.float64, device="cuda")
+    dummy3 = torch.empty(16, dtype=torch.float64, device="cuda")
     st = lbm.lbm_step_fixed_scratch(ref.lat, ref.sp, ref.mech, dummy.data_ptr(), dummy2.data_ptr(),
-                                    dummy.data_ptr(), torch.cuda.current_stream().cuda_stream)
+                                    dummy3.data_ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == lbm.LBM_ERR_ARG
+    ref.close()
+
+
+def test_fixed_scratch_rejects_overlapping_buffers(lbm):
+    """The temperature row is copied into the array before the step and back
+    after it; a T_io inside either population buffer, or population buffers
+    that overlap, would corrupt the state, so the call refuses them before
+    any device work."""
+    import torch
+    prob = w.config1_problem()
+    ref = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    stream = torch.cuda.current_stream().cuda_stream
+    pop, T = _current_state(ref, lbm)
+    n_pop = pop.numel()
+    pop_in, pop_out = pop.clone(), torch.empty_like(pop)
+    both = torch.empty(n_pop + ref.N, dtype=torch.float64, device="cuda")
+    T_io = T.clone()
+    bad = [(pop_in, pop_out, pop_in[5:5 + ref.N]),                 # T_io inside pop_in
+           (pop_in, pop_out, pop_out[n_pop - ref.N // 2:]),        # T_io runs into pop_out's tail
+           (both[:n_pop], both[ref.N:], T_io)]                     # population buffers overlap
+    before = pop_in.clone()
+    for a, b, t in bad:
+        st = lbm.lbm_step_fixed_scratch(ref.lat, ref.sp, ref.mech, a.data_ptr(), b.data_ptr(), t.data_ptr(), stream)
+        assert st == lbm.LBM_ERR_ARG
+    torch.cuda.synchronize()
+    assert torch.equal(pop_in, before)
     ref.close()
