@@ -65,6 +65,8 @@ def _bind(L):
     L.orc_rates.argtypes = [C.c_void_p, _dp, C.c_double, _dp]
     L.orc_heat_release.restype = C.c_double
     L.orc_heat_release.argtypes = [C.c_void_p, _dp, C.c_double]
+    L.orc_total_heat_release.restype = C.c_double
+    L.orc_total_heat_release.argtypes = [C.c_void_p, _ip]
     L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
     L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
     L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
@@ -211,6 +213,13 @@ class Oracle:
         """hdot^c = -sum_a H_a rho_dot_a at one node state (Sec. 5b)."""
         rho_a = np.ascontiguousarray(rho_a, dtype=np.float64)
         return float(self._L.orc_heat_release(self._h, _d(rho_a), float(T)))
+
+    def total_heat_release(self):
+        """Sum over the lattice of hdot^c at the current time level (Sec. 5b)."""
+        st = C.c_int(0)
+        J = float(self._L.orc_total_heat_release(self._h, C.byref(st)))
+        assert st.value == 0, st.value
+        return J
 
     def diffusion_velocities(self, Y, ua_minus_u, T):
         Y = np.ascontiguousarray(Y, dtype=np.float64)

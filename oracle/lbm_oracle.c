@@ -866,6 +866,18 @@ double orc_heat_release(const orc_state *s, const double *rho_a, double T)
     return h;
 }
 
+/* Heat release summed over the lattice at the current time level (the
+ * state the next collision sees: pulled populations, their moments and
+ * temperature), Sec. 5b.  *status receives the moment pass's status. */
+double orc_total_heat_release(orc_state *s, int *status)
+{
+    int st = stream_and_moments(s);
+    if (status) *status = st;
+    double J = 0.0;
+    for (int n = 0; n < s->N; ++n) J += orc_heat_release(s, s->rho_a + (size_t)n * s->M, s->T[n]);
+    return J;
+}
+
 /* Diffusion velocities du[M][3] from Eq. (transform1) at a node state. */
 int orc_diffusion_velocities(const orc_state *s, const double *Y, const double *ua_minus_u, double T, double *du)
 {
