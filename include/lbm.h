@@ -278,7 +278,9 @@ size_t lbm_moments_count(const lbm_ctx *ctx, unsigned mask);
  * the step (the paper has none; the transposed step is not part of this
  * library).  The second population buffer serves as scratch, as in
  * lbm_moments.  Waits for the stream; returns like lbm_sync, or
- * LBM_ERR_ARG for a NULL ctx or J. */
+ * LBM_ERR_ARG for a NULL ctx or J.  The transposed step is
+ * lbm_adjoint_step and the gradient through time
+ * lbm_heat_release_gradient. */
 int lbm_heat_release(lbm_ctx *ctx, double *J, double *dJ_dlogA, double *dJ_dT, double *dJ_drho);
 
 /* Gradient of the same objective J = sum over the nodes of hdot^c with
@@ -295,6 +297,61 @@ int lbm_heat_release(lbm_ctx *ctx, double *J, double *dJ_dlogA, double *dJ_dT, d
  * batches).  The second population buffer serves as scratch.  Waits for
  * the stream; returns like lbm_sync. */
 int lbm_heat_release_adjoint(lbm_ctx *ctx, double *dJ_dF);
+
+/* Hand-written adjoint of the double-precision step (the paper has no
+ * adjoint; the objective is its heat release rate of Sec. 5b).  Both calls
+ * below take a caller-owned device workspace of at least the size this
+ * call reports, for nsteps steps with a checkpoint every checkpoint_every
+ * steps (nsteps = 0: the size lbm_adjoint_step needs).  LBM_ERR_ARG for a
+ * NULL ctx or bytes, or negative counts. */
+int lbm_adjoint_workspace_bytes(const lbm_ctx *ctx, int nsteps, int checkpoint_every, size_t *bytes);
+
+/* One reverse step at the current state F (the state the next lbm_step
+ * would pull from): given lam_next = dL/dF' for the state F' = step(F)
+ * that lbm_step would produce, returns
+ *   lam = (dF'/dF)^T lam_next  (+ dJ_t/dF with with_objective != 0)
+ * where J_t is the sum over the nodes of hdot^c at the state the step's
+ * collision sees (as lbm_heat_release at F).  The transpose covers every
+ * dependence of F' on F: the pull (Eqs. (finalNumericalEquations), (f),
+ * (g) left-hand sides), the moments and slaving (Eqs. (Pa), (strongest)),
+ * the Newton temperature (Eq. (temperature), implicit-function adjoint),
+ * the relaxation rates (Eqs. (mu), (lambda), (tauab), (fStar)), the
+ * Stefan-Maxwell solve (Eq. (transform1); B is symmetric after the
+ * Y-scaling, so its adjoint solve is with B itself), the production rates
+ * (Sec. 4), the isotropy correction and the interdiffusion heat flux with
+ * their lattice gradients (Eqs. (Xalpha), (Ai), (qdiff), (corrFourier))
+ * and the three collisions.
+ *   lam_next, lam  device, double [M+1][27][N] (lbm_get_populations layout);
+ *                  distinct, and neither inside the workspace
+ *   dJ_dlogA       host, double [R], or NULL: (dF'/d ln A_k)^T lam_next
+ *                  (+ dJ_t/d ln A_k)
+ *   workspace      device, at least lbm_adjoint_workspace_bytes(ctx, 0, 1)
+ * The state is not changed.  LBM_FP64 periodic lattices only
+ * (LBM_ERR_UNSUPPORTED otherwise).  Waits for the stream; returns like
+ * lbm_sync. */
+int lbm_adjoint_step(lbm_ctx *ctx, const double *lam_next, double *lam, double *dJ_dlogA, int with_objective,
+                     void *workspace, size_t workspace_bytes);
+
+/* The objective integrated over time, J = sum_{t=0}^{nsteps-1} J_t with
+ * J_t = sum over the nodes of hdot^c at the state step t's collision sees,
+ * starting from the current state, which must be one lbm_init made with
+ * zero velocity; and its gradients through the dynamics:
+ *   J          host, double: the objective
+ *   dJ_dlogA   host, double [R], or NULL: dJ/d ln A_k (A_k as in
+ *              lbm_heat_release)
+ *   dJ_dT0     host or device, double [N], or NULL: dJ/dT(x, 0), the
+ *              initial temperature of each node at fixed mole fractions,
+ *              pressure and zero velocity (the inputs of lbm_init)
+ * The forward sweep keeps the state every checkpoint_every steps; the
+ * reverse sweep recomputes each segment's states from its checkpoint and
+ * applies lbm_adjoint_step's transpose step by step, last step first.  The
+ * context ends at the state after nsteps steps, as lbm_step(nsteps) leaves
+ * it.  LBM_FP64 periodic lattices only (LBM_ERR_UNSUPPORTED otherwise);
+ * LBM_ERR_ARG for nsteps < 1, checkpoint_every < 1 or a workspace smaller
+ * than lbm_adjoint_workspace_bytes(ctx, nsteps, checkpoint_every).  Waits
+ * for the stream; returns like lbm_sync. */
+int lbm_heat_release_gradient(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J, double *dJ_dlogA,
+                              double *dJ_dT0, void *workspace, size_t workspace_bytes);
 
 /* The step's chemistry at n given node states, for checks of the node
  * functions on inputs of the caller's choice.  Inputs, device:

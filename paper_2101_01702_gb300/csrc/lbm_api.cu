@@ -6,6 +6,7 @@
 // CUDA-graph replay, and status reporting.  Every step of the numerical
 // method runs in the kernels of k_fp64.cu, k_mixed.cu and k_mixed_fast.cu.
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -226,6 +227,77 @@ void references_from_stats(MechConst &mc, int M, const double *st, size_t N)
 }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+// Workspace of the adjoint calls, in doubles from a 256-byte aligned base:
+// every region starts on a 256-byte boundary.
+struct AdjLayout {
+    size_t tkeep, fbar, mbar, coef, aux, theta, theta_out;     // one reverse step
+    size_t lamA, lamB, ck, ckT, seg, segT, jpart, hrrpart, dT0;  // gradient through time
+    size_t total;                                                // bytes
+    int nck;
+};
+
+AdjLayout adj_layout(const lbm_ctx *c, int nsteps, int every)
+{
+    const size_t N = (size_t)c->N, pop = (size_t)c->S * LBMK_Q * N, R = (size_t)std::max(c->mc.R, 1);
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        const size_t at = off;
+        off += (n + 31) & ~(size_t)31;
+        return at;
+    };
+    AdjLayout L;
+    L.tkeep = take(N);
+    L.fbar = take(pop);
+    L.mbar = take((size_t)adj_mbar_rows(c->M) * N);
+    L.coef = take((size_t)c->M * N);
+    L.aux = take(10 * N);
+    L.theta = take((size_t)adj_blocks(c->N) * R);
+    L.theta_out = take(R);
+    L.nck = nsteps > 0 ? (nsteps + every - 1) / every : 0;
+    if (nsteps > 0) {
+        L.lamA = take(pop);
+        L.lamB = take(pop);
+        L.ck = take((size_t)L.nck * pop);
+        L.ckT = take((size_t)L.nck * N);
+        L.seg = take((size_t)every * pop);
+        L.segT = take((size_t)every * N);
+        L.jpart = take((size_t)nsteps * (1 + R));
+        L.hrrpart = take((size_t)lbmk::hrr_blocks(c->N) * (1 + R));
+        L.dT0 = take(N);
+    } else {
+        L.lamA = L.lamB = L.ck = L.ckT = L.seg = L.segT = L.jpart = L.hrrpart = L.dT0 = 0;
+    }
+    L.total = off * sizeof(double);
+    return L;
+}
+
+// LBM_OK when the adjoint supports context c (double precision, one periodic lattice).
+int adjoint_supported(const lbm_ctx *c)
+{
+    if (c->lat.precision != LBM_FP64 || c->lat.bc_x != LBM_BC_PERIODIC || c->nseg > 1) return LBM_ERR_UNSUPPORTED;
+    return LBM_OK;
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+int copy_d2d(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    return check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+}
+
+// The record of the step at a.src (moments, temperature, relaxation,
+// Stefan-Maxwell solve; then G), as the forward step's first passes form it.
+int adj_record(const StepArgs &a)
+{
+    int e = lbmk::launch_one_fp64(a, LBMK_K_PRE);
+    if (!e) e = lbmk::launch_one_fp64(a, LBMK_K_GRAD);
+    return e;
+}
 
 }  // namespace
 
@@ -699,6 +771,176 @@ int lbm_heat_release_adjoint(lbm_ctx *c, double *dJ_dF)
         }
     }
     return lbm_sync(c);
+}
+
+int lbm_adjoint_workspace_bytes(const lbm_ctx *c, int nsteps, int every, size_t *bytes)
+{
+    if (!c || !bytes || nsteps < 0 || every < 1) return LBM_ERR_ARG;
+    *bytes = adj_layout(c, nsteps, every).total + 256;      // room to align the caller's base
+    return LBM_OK;
+}
+
+namespace {
+double *ws_base(void *ws) { return (double *)(((uintptr_t)ws + 255) & ~(uintptr_t)255); }
+
+AdjBufs adj_bufs(double *w, const AdjLayout &L)
+{
+    AdjBufs g;
+    g.lam_next = nullptr;
+    g.lam = nullptr;
+    g.fbar = w + L.fbar;
+    g.mbar = w + L.mbar;
+    g.coef = w + L.coef;
+    g.aux = w + L.aux;
+    g.theta = w + L.theta;
+    g.with_objective = 1;
+    return g;
+}
+}  // namespace
+
+int lbm_adjoint_step(lbm_ctx *c, const double *lam_next, double *lam, double *dJ_dlogA, int with_objective,
+                     void *workspace, size_t workspace_bytes)
+{
+    if (!c || !lam_next || !lam || !workspace || lam_next == lam) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    const int sup = adjoint_supported(c);
+    if (sup != LBM_OK) return sup;
+    const AdjLayout L = adj_layout(c, 0, 1);
+    const size_t N = (size_t)c->N, popb = (size_t)c->S * LBMK_Q * N * sizeof(double);
+    const int R = c->mc.R;
+    if (workspace_bytes < L.total + 256 || !is_device_ptr(workspace) || !is_device_ptr(lam_next) ||
+        !is_device_ptr(lam))
+        return LBM_ERR_ARG;
+    if (ranges_overlap(lam_next, popb, lam, popb) || ranges_overlap(lam_next, popb, workspace, workspace_bytes) ||
+        ranges_overlap(lam, popb, workspace, workspace_bytes))
+        return LBM_ERR_ARG;
+    double *w = ws_base(workspace);
+    double *Trow = c->macro + (size_t)DR_T * N;
+    const cudaStream_t s = c->stream;
+    // The record pass overwrites the temperature row (the Newton starting
+    // point of the next step); it is kept aside and put back.
+    int st = copy_d2d(w + L.tkeep, Trow, N * sizeof(double), s);
+    const int nb = adj_blocks(c->N);
+    if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(w + L.theta, 0, (size_t)nb * std::max(R, 1) * sizeof(double), s));
+    if (st != LBM_OK) return st;
+    if (lbmk::adj_upload(c->slot, c->mc, s)) return LBM_ERR_CUDA;
+    const StepArgs a = args_of(c);
+    AdjBufs g = adj_bufs(w, L);
+    g.lam_next = lam_next;
+    g.lam = lam;
+    g.with_objective = with_objective ? 1 : 0;
+    if (adj_record(a) || lbmk::adj_step_fp64(a, g)) return LBM_ERR_CUDA;
+    if (lbmk::column_sums_fp64(w + L.theta, nb, R, w + L.theta_out, s)) return LBM_ERR_CUDA;
+    double hA[LBMK_MAXR];
+    if (dJ_dlogA && R > 0) st = check_cuda(cudaMemcpyAsync(hA, w + L.theta_out, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (st == LBM_OK) st = copy_d2d(Trow, w + L.tkeep, N * sizeof(double), s);
+    if (st == LBM_OK) st = lbm_sync(c);
+    if (st != LBM_OK) return st;
+    if (dJ_dlogA)
+        for (int k = 0; k < R; ++k) dJ_dlogA[k] = hA[k];
+    return LBM_OK;
+}
+
+int lbm_heat_release_gradient(lbm_ctx *c, int nsteps, int every, double *J, double *dJ_dlogA, double *dJ_dT0,
+                              void *workspace, size_t workspace_bytes)
+{
+    if (!c || !J || !workspace || nsteps < 1 || every < 1) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    const int sup = adjoint_supported(c);
+    if (sup != LBM_OK) return sup;
+    const AdjLayout L = adj_layout(c, nsteps, every);
+    if (workspace_bytes < L.total + 256 || !is_device_ptr(workspace)) return LBM_ERR_ARG;
+    const bool T0_dev = dJ_dT0 && is_device_ptr(dJ_dT0);
+    const size_t N = (size_t)c->N, pop = (size_t)c->S * LBMK_Q * N, popb = pop * sizeof(double);
+    if (T0_dev && ranges_overlap(dJ_dT0, N * sizeof(double), workspace, workspace_bytes)) return LBM_ERR_ARG;
+    const int R = c->mc.R, W = 1 + R;
+    const lbmk::PrecisionOps &op = ops(c->lat.precision);
+    const cudaStream_t s = c->stream;
+    double *w = ws_base(workspace);
+    double *Trow = c->macro + (size_t)DR_T * N;
+    const size_t Tb = N * sizeof(double);
+    int st = LBM_OK;
+
+    // Forward sweep: J_t at every step, the state and temperature row every
+    // checkpoint_every steps.
+    for (int t = 0; t < nsteps && st == LBM_OK; ++t) {
+        if (t % every == 0) {
+            const int k = t / every;
+            st = copy_d2d(w + L.ck + (size_t)k * pop, c->buf[c->cur], popb, s);
+            if (st == LBM_OK) st = copy_d2d(w + L.ckT + (size_t)k * N, Trow, Tb, s);
+            if (st != LBM_OK) break;
+        }
+        if (op.hrr(args_of(c), R, nullptr, nullptr, w + L.hrrpart, w + L.jpart + (size_t)t * W)) st = LBM_ERR_CUDA;
+        if (st == LBM_OK && op.step(args_of(c), nullptr)) st = LBM_ERR_CUDA;
+        c->cur = 1 - c->cur;
+    }
+    if (st == LBM_OK) st = copy_d2d(w + L.tkeep, Trow, Tb, s);
+    if (st == LBM_OK) st = lbm_sync(c);                  // a failed forward sweep stops here
+    if (st != LBM_OK) return st;
+
+    // Reverse sweep, segment by segment from the last.
+    if (lbmk::adj_upload(c->slot, c->mc, s)) return LBM_ERR_CUDA;
+    double *lamA = w + L.lamA, *lamB = w + L.lamB;
+    const int nb = adj_blocks(c->N);
+    st = check_cuda(cudaMemsetAsync(lamA, 0, popb, s));
+    if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(w + L.theta, 0, (size_t)nb * std::max(R, 1) * sizeof(double), s));
+    AdjBufs g = adj_bufs(w, L);
+    for (int k = L.nck - 1; k >= 0 && st == LBM_OK; --k) {
+        const int t0 = k * every, len = std::min(every, nsteps - t0);
+        double *seg = w + L.seg, *segT = w + L.segT;
+        st = copy_d2d(seg, w + L.ck + (size_t)k * pop, popb, s);
+        if (st == LBM_OK) st = copy_d2d(segT, w + L.ckT + (size_t)k * N, Tb, s);
+        for (int j = 0; j + 1 < len && st == LBM_OK; ++j) {      // the segment's states, recomputed
+            st = copy_d2d(Trow, segT + (size_t)j * N, Tb, s);
+            StepArgs a = args_of(c);
+            a.src = seg + (size_t)j * pop;
+            a.dst = seg + (size_t)(j + 1) * pop;
+            if (st == LBM_OK && op.step(a, nullptr)) st = LBM_ERR_CUDA;
+            if (st == LBM_OK) st = copy_d2d(segT + (size_t)(j + 1) * N, Trow, Tb, s);
+        }
+        for (int j = len - 1; j >= 0 && st == LBM_OK; --j) {       // last step first
+            st = copy_d2d(Trow, segT + (size_t)j * N, Tb, s);
+            StepArgs a = args_of(c);
+            a.src = seg + (size_t)j * pop;
+            g.lam_next = lamA;
+            g.lam = lamB;
+            if (st == LBM_OK && (adj_record(a) || lbmk::adj_step_fp64(a, g))) st = LBM_ERR_CUDA;
+            std::swap(lamA, lamB);
+        }
+    }
+    // lamA is now dJ/dF of the initial state: carry it to T(x, 0)
+    double *dT0 = T0_dev ? dJ_dT0 : w + L.dT0;
+    if (st == LBM_OK && dJ_dT0) {
+        st = copy_d2d(Trow, w + L.ckT, Tb, s);
+        StepArgs a = args_of(c);
+        a.src = w + L.ck;
+        if (st == LBM_OK && lbmk::adj_init_T_fp64(a, lamA, dT0)) st = LBM_ERR_CUDA;
+        if (st == LBM_OK && !T0_dev)
+            st = check_cuda(cudaMemcpyAsync(dJ_dT0, dT0, Tb, cudaMemcpyDeviceToHost, s));
+    }
+    if (st == LBM_OK && lbmk::column_sums_fp64(w + L.theta, nb, R, w + L.theta_out, s)) st = LBM_ERR_CUDA;
+    double hA[LBMK_MAXR];
+    double *hJ = (double *)malloc((size_t)nsteps * W * sizeof(double));
+    if (!hJ) st = st == LBM_OK ? LBM_ERR_ARG : st;
+    if (st == LBM_OK && R > 0)
+        st = check_cuda(cudaMemcpyAsync(hA, w + L.theta_out, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (st == LBM_OK)
+        st = check_cuda(cudaMemcpyAsync(hJ, w + L.jpart, (size_t)nsteps * W * sizeof(double),
+                                        cudaMemcpyDeviceToHost, s));
+    const int st_r = copy_d2d(Trow, w + L.tkeep, Tb, s);      // the temperature row after the forward sweep
+    if (st == LBM_OK) st = st_r;
+    if (st == LBM_OK) st = lbm_sync(c);
+    if (st == LBM_OK) {
+        double acc = 0.0;
+        for (int t = 0; t < nsteps; ++t) acc += hJ[(size_t)t * W];
+        *J = acc;
+        if (dJ_dlogA)
+            for (int k = 0; k < R; ++k) dJ_dlogA[k] = hA[k];
+    }
+    free(hJ);
+    return st;
 }
 
 int lbm_chemistry_at(lbm_ctx *c, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,

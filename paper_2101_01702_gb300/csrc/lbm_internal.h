@@ -221,3 +221,41 @@ struct PrecisionOps {
     int (*hrr_adj_gather)(const StepArgs &a, const double *adj, int s, double *out);
 };
 }  // namespace lbmk
+
+// Hand-written adjoint of the double-precision step (periodic lattices).
+// One reverse step takes lam_next, the adjoint of the post-collision state
+// the step writes, and returns lam, the adjoint of the state it pulls from
+// (plus, with with_objective, the gradient of sum_nodes hdot^c at the
+// state the step's collision sees).  The per-node record of the step must
+// have been recomputed first (the moment and gradient passes of the
+// forward step, launch_one_fp64 LBMK_K_PRE and LBMK_K_GRAD, on the same
+// state and Newton starting temperatures).  The adjoint kernels live in a
+// unit of their own (k_adjoint.cu) whose constant-memory tables adj_upload
+// fills, in the context's slot, before each adjoint call.
+//   mbar  [adj_mbar_rows(M)][N]: adjoint of the pulled moments (rho_a and
+//         j_a of the M-1 stored species, rho, j, the pressure tensor's six
+//         entries, rho E, q)
+//   coef  [M][N]: 1 - 2 beta_a (a < M-1) and 1 - omega
+//   aux   [10][N]: adjoints of X (3) and of sum_a H_a grad Y_a (3), then
+//         (1/omega - 1/2) times the adjoint of G (3) and the adjoint of
+//         1/omega - 1/2 (1)
+//   theta [adj_blocks(N)][R]: per-block sums of the ln A_k gradient, which
+//         every reverse step adds to
+#define LBMK_ADJ_THREADS 128
+__host__ __device__ constexpr int adj_mbar_rows(int M) { return 4 * (M - 1) + 14; }
+inline int adj_blocks(long long N) { return (int)((N + LBMK_ADJ_THREADS - 1) / LBMK_ADJ_THREADS); }
+struct AdjBufs {
+    const double *lam_next;
+    double *lam, *fbar, *mbar, *coef, *aux, *theta;
+    int with_objective;
+};
+namespace lbmk {
+int adj_upload(int slot, const MechConst &mc, cudaStream_t s);
+int adj_step_fp64(const StepArgs &a, const AdjBufs &g);
+// d J / d T(x, 0) of a state made by lbm_init (every set at equilibrium at
+// zero velocity, fixed mole fractions and pressure) from the adjoint lam0 of
+// that state: out [N]
+int adj_init_T_fp64(const StepArgs &a, const double *lam0, double *out);
+// column sums of nb partial records of width w (fixed order)
+int column_sums_fp64(const double *partial, int nb, int w, double *out, cudaStream_t s);
+}  // namespace lbmk

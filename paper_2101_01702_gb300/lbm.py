@@ -102,7 +102,8 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
-            "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe"]
+            "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe",
+            "lbm_adjoint_workspace_bytes", "lbm_adjoint_step", "lbm_heat_release_gradient"]
 
 
 def library_path() -> str:
@@ -240,6 +241,36 @@ def lbm_exp_check(x_ptr: int, y_ptr: int, y_ref_ptr: int, n: int, stream: int) -
     """The kernels' exponential into y and CUDA's exp into y_ref (device)."""
     return _lib.lbm_exp_check(C.c_void_p(x_ptr), C.c_void_p(y_ptr), C.c_void_p(y_ref_ptr), int(n),
                               C.c_void_p(stream))
+
+
+_lib.lbm_adjoint_workspace_bytes.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_size_t)]
+_lib.lbm_adjoint_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_int, C.c_void_p, C.c_size_t]
+_lib.lbm_heat_release_gradient.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, C.c_void_p, C.c_void_p,
+                                           C.c_size_t]
+
+
+def lbm_adjoint_workspace_bytes(ctx, nsteps: int, checkpoint_every: int) -> int:
+    out = C.c_size_t(0)
+    _check(_lib.lbm_adjoint_workspace_bytes(ctx, int(nsteps), int(checkpoint_every), C.byref(out)),
+           "lbm_adjoint_workspace_bytes")
+    return int(out.value)
+
+
+def lbm_adjoint_step(ctx, lam_next_ptr: int, lam_ptr: int, dlogA, with_objective: bool, ws_ptr: int,
+                     ws_bytes: int) -> int:
+    """One reverse step at the current state (see include/lbm.h); dlogA: numpy [R] or None."""
+    return _lib.lbm_adjoint_step(ctx, C.c_void_p(lam_next_ptr), C.c_void_p(lam_ptr),
+                                 dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
+                                 1 if with_objective else 0, C.c_void_p(ws_ptr), int(ws_bytes))
+
+
+def lbm_heat_release_gradient(ctx, nsteps: int, checkpoint_every: int, J: np.ndarray, dlogA, dT0_ptr,
+                              ws_ptr: int, ws_bytes: int) -> int:
+    """Time-integrated heat release and its gradients (see include/lbm.h)."""
+    return _lib.lbm_heat_release_gradient(ctx, int(nsteps), int(checkpoint_every), J.ctypes.data_as(_dp),
+                                          dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
+                                          C.c_void_p(dT0_ptr) if dT0_ptr else None, C.c_void_p(ws_ptr),
+                                          int(ws_bytes))
 
 
 _lib.lbm_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, _dp, C.c_void_p]
@@ -490,6 +521,41 @@ class Solver:
             _check(lbm_heat_release_adjoint(self.ctx, out.ctypes.data), "lbm_heat_release_adjoint")
         return out
 
+    def _workspace(self, nsteps: int, every: int):
+        nb = lbm_adjoint_workspace_bytes(self.ctx, nsteps, every)
+        return self.torch.empty(nb, dtype=self.torch.uint8, device=self.device), nb
+
+    @_on_device
+    def adjoint_step(self, lam_next, with_objective: bool = True):
+        """One reverse step at the current state: lam_next, a float64 device
+        tensor [M+1, 27, N] (the adjoint of the state the next step would
+        produce), gives (lam [M+1, 27, N] on the device, d/d ln A_k [R] numpy)
+        -- see lbm_adjoint_step.  The state is not changed."""
+        torch = self.torch
+        lam_next = lam_next.contiguous().to(device=self.device, dtype=torch.float64)
+        lam = torch.empty_like(lam_next)
+        ws, nb = self._workspace(0, 1)
+        dA = np.zeros(max(self.R, 1))
+        _check(lbm_adjoint_step(self.ctx, lam_next.data_ptr(), lam.data_ptr(), dA, with_objective, ws.data_ptr(), nb),
+               "lbm_adjoint_step")
+        return lam, dA[:self.R]
+
+    @_on_device
+    def heat_release_gradient(self, steps: int, checkpoint_every: int = 64):
+        """J = sum over steps and nodes of hdot^c from the current (freshly
+        initialised) state, with dJ/d ln A_k [R] (numpy) and dJ/dT(x, 0) [N]
+        (float64 device tensor); see lbm_heat_release_gradient.  Also returns
+        the workspace size in bytes."""
+        torch = self.torch
+        ws, nb = self._workspace(steps, checkpoint_every)
+        J = np.zeros(1)
+        dA = np.zeros(max(self.R, 1))
+        dT0 = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        _check(lbm_heat_release_gradient(self.ctx, steps, checkpoint_every, J, dA, dT0.data_ptr(), ws.data_ptr(), nb),
+               "lbm_heat_release_gradient")
+        del ws
+        return float(J[0]), dA[:self.R], dT0, nb
+
     @_on_device
     def chemistry_at(self, rho_a, T):
         """The step's chemistry at given node states: rho_a [M, n], T [n]
@@ -532,3 +598,52 @@ class Solver:
         out = np.empty((self.S, 27, self.N), dtype=np.float64)
         _check(lbm_get_populations(self.ctx, out), "lbm_get_populations")
         return out
+
+
+# ---------------------------------------------------------------------------
+# Gradients of the time-integrated heat release as a torch.autograd.Function
+# ---------------------------------------------------------------------------
+def _heat_release_function():
+    import torch
+
+    class HeatReleaseObjective(torch.autograd.Function):
+        """J(ln A, T0) = sum_{t < steps} sum_nodes hdot^c (Sec. 5b) of a
+        periodic double-precision lattice started by lbm_init from the
+        problem's mole fractions, pressure and zero velocity at T(x, 0) = T0.
+        forward runs lbm_heat_release_gradient (forward sweep with
+        checkpoints every checkpoint_every steps, then the hand-written
+        reverse sweep); backward scales the stored gradients by the incoming
+        gradient.  Inputs: log_A [R] and T0 [N] float64 tensors."""
+
+        @staticmethod
+        def forward(ctx, log_A, T0, problem, steps, checkpoint_every):
+            import copy
+            mech = copy.deepcopy(problem.mech)
+            mech.log_A = log_A.detach().cpu().numpy().astype(np.float64)
+            dev = T0.device if T0.is_cuda else torch.device("cuda", torch.cuda.current_device())
+            s = Solver(problem.lattice, problem.species, mech, LBM_FP64, device=dev)
+            try:
+                s.init(problem.init.X, T0.detach().cpu().numpy().astype(np.float64), None, problem.init.P)
+                J, dA, dT0, _ = s.heat_release_gradient(int(steps), int(checkpoint_every))
+            finally:
+                s.close()
+            ctx.save_for_backward(torch.from_numpy(dA).to(log_A.device), dT0.to(T0.device))
+            return torch.tensor(J, dtype=torch.float64, device=T0.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dA, dT0 = ctx.saved_tensors
+            return gJ * dA, gJ * dT0, None, None, None
+
+    return HeatReleaseObjective
+
+
+_HRO = None
+
+
+def heat_release_objective(log_A, T0, problem, steps: int, checkpoint_every: int = 64):
+    """Differentiable time-integrated heat release (HeatReleaseObjective.apply)."""
+    global _HRO
+    if _HRO is None:
+        _HRO = _heat_release_function()
+    return _HRO.apply(log_A, T0, problem, steps, checkpoint_every)

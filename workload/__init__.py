@@ -11,6 +11,7 @@ from .problem import Problem, LatticeSpec, SpeciesSpec, MechanismSpec, InitField
 from .configs import (  # noqa: F401
     config1_problem,
     flame1d_problem,
+    adjoint_flame_problem,
     sphere3d_problem,
     small_periodic_problem,
     batched_flames_lengths,

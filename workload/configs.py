@@ -313,6 +313,18 @@ def flame1d_problem(nx: int = 4096, ny: int = 4, nz: int = 4, phi: float = 1.0,
                    sp, mech, InitFields(X=X, T=T, u=None, P=mech.P0), steps=20000)
 
 
+def adjoint_flame_problem(nx: int = 512, ny: int = 4, nz: int = 4, T_slab: float = 1500.0,
+                          chem_scale: float = MECH9_CHEM_SCALE) -> Problem:
+    """The quasi-1D flame tube of flame1d_problem (phi = 1 unburnt mixture
+    at 300 K, the rightmost fifth at T_slab) with periodic x faces: the
+    workload of the heat-release gradients through time."""
+    p = flame1d_problem(nx=nx, ny=ny, nz=nz, T_slab=T_slab, chem_scale=chem_scale)
+    p.lattice.bc_x = BC_PERIODIC
+    p.name = f"adjoint_flame_{nx}x{ny}x{nz}_M9_periodic"
+    p.steps = 2000
+    return p
+
+
 def sphere3d_problem(n: int = 256, radius: float = 20.0, T_u: float = MECH9_T_UNBURNT,
                      T_hot: float = 2000.0, seed: int = 1703,
                      chem_scale: float = MECH9_CHEM_SCALE, shape=None) -> Problem:
