@@ -101,6 +101,42 @@ def fp64_probe(lbm, torch, stream, blocks_per_sm: int = 8):
                    f"(2 flop each), 4 independent exp / log chains per thread; CUDA events"}
 
 
+def adjoint_timing(lbm, torch, steps: int = 2000, every: int = 64, nx: int = 512):
+    """Gradients of the time-integrated heat release through the dynamics on
+    the periodic quasi-1D flame (nx x 4 x 4, nine species, double): the
+    objective alone (forward sweep) against the objective with dJ/d ln A_k
+    and dJ/dT(x, 0) (forward sweep with checkpoints, reverse sweep with
+    recomputation), host-timed around calls that end with a stream wait;
+    peak device memory of the solver and workspace."""
+    import workload as w
+    prob = w.adjoint_flame_problem(nx=nx)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    base = torch.cuda.memory_allocated()
+    torch.cuda.reset_peak_memory_stats()
+    s = lbm.Solver.from_problem(prob, precision=lbm.LBM_FP64)
+    s.heat_release_gradient(8, 4)                               # warm-up of every kernel
+    s.init(prob.init.X, prob.init.T, None, prob.init.P)
+    t0 = time.perf_counter()
+    J_fwd = s.heat_release_total(steps)
+    t_fwd = time.perf_counter() - t0
+    s.init(prob.init.X, prob.init.T, None, prob.init.P)
+    t0 = time.perf_counter()
+    J, dA, dT0, ws = s.heat_release_gradient(steps, every)
+    t_all = time.perf_counter() - t0
+    peak = torch.cuda.max_memory_allocated() - base
+    gT = dT0.abs().max().item()
+    s.close()
+    del s, dT0
+    torch.cuda.empty_cache()
+    return {"workload": prob.name, "nodes": prob.lattice.n_nodes, "steps": steps, "checkpoint_every": every,
+            "forward_s": t_fwd, "forward_and_backward_s": t_all, "backward_over_forward": (t_all - t_fwd) / t_fwd,
+            "peak_device_bytes": int(peak), "workspace_bytes": int(ws), "J": J, "J_forward_only": J_fwd,
+            "max_abs_dJ_dlogA": float(np.abs(dA).max()), "max_abs_dJ_dT0": gT,
+            "note": "lbm_heat_release_gradient: J = sum over steps and nodes of hdot^c; gradients with respect "
+                    "to the 21 ln A_k and T(x, 0); FP64"}
+
+
 def stored_bytes_per_node(M: int, mixed: bool) -> int:
     """Bytes of one copy of the stored state per node: in mixed precision the
     26 moving populations of the M species/mixture sets in float, their rest
@@ -487,6 +523,10 @@ def run_ours(args):
         del s64
         torch.cuda.empty_cache()
 
+    adjoint = None
+    if not args.skip_adjoint:
+        adjoint = adjoint_timing(lbm, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = _cpu_oracle_sample()
@@ -517,6 +557,7 @@ def run_ours(args):
             "mixed_fast_step": fast,
             "fp64_step": fp64,
             "heat_release": hrr,
+            "adjoint": adjoint,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -683,6 +724,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-hrr", action="store_true", help="skip the heat-release sensitivity measurement")
+    ap.add_argument("--skip-adjoint", action="store_true", help="skip the gradients through time (512x4x4, 2000 steps)")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
     ap.add_argument("--cpu-legs", action="store_true",
                     help="instead of timing the GPU: the oracle's timed legs (64x4x4 200 steps, 32^3 1000 steps, "

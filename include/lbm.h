@@ -302,8 +302,9 @@ int lbm_heat_release_adjoint(lbm_ctx *ctx, double *dJ_dF);
  * adjoint; the objective is its heat release rate of Sec. 5b).  Both calls
  * below take a caller-owned device workspace of at least the size this
  * call reports, for nsteps steps with a checkpoint every checkpoint_every
- * steps (nsteps = 0: the size lbm_adjoint_step needs).  LBM_ERR_ARG for a
- * NULL ctx or bytes, or negative counts. */
+ * steps (nsteps = 0: the size lbm_adjoint_step needs; checkpoint_every = 0:
+ * the size of the objective alone, without gradients).  LBM_ERR_ARG for a
+ * NULL ctx or bytes, negative counts, or both counts 0. */
 int lbm_adjoint_workspace_bytes(const lbm_ctx *ctx, int nsteps, int checkpoint_every, size_t *bytes);
 
 /* One reverse step at the current state F (the state the next lbm_step
@@ -344,7 +345,10 @@ int lbm_adjoint_step(lbm_ctx *ctx, const double *lam_next, double *lam, double *
  *              pressure and zero velocity (the inputs of lbm_init)
  * The forward sweep keeps the state every checkpoint_every steps; the
  * reverse sweep recomputes each segment's states from its checkpoint and
- * applies lbm_adjoint_step's transpose step by step, last step first.  The
+ * applies lbm_adjoint_step's transpose step by step, last step first.  With
+ * dJ_dlogA and dJ_dT0 both NULL only the forward sweep runs (J alone,
+ * without checkpoints; the workspace needs only
+ * lbm_adjoint_workspace_bytes(ctx, nsteps, 0)).  The
  * context ends at the state after nsteps steps, as lbm_step(nsteps) leaves
  * it.  LBM_FP64 periodic lattices only (LBM_ERR_UNSUPPORTED otherwise);
  * LBM_ERR_ARG for nsteps < 1, checkpoint_every < 1 or a workspace smaller

@@ -254,19 +254,21 @@ AdjLayout adj_layout(const lbm_ctx *c, int nsteps, int every)
     L.aux = take(10 * N);
     L.theta = take((size_t)adj_blocks(c->N) * R);
     L.theta_out = take(R);
-    L.nck = nsteps > 0 ? (nsteps + every - 1) / every : 0;
+    // every = 0: the objective alone (no checkpoints, no reverse sweep)
+    L.nck = nsteps > 0 && every > 0 ? (nsteps + every - 1) / every : 0;
+    L.lamA = L.lamB = L.ck = L.ckT = L.seg = L.segT = L.jpart = L.hrrpart = L.dT0 = 0;
     if (nsteps > 0) {
+        L.jpart = take((size_t)nsteps * (1 + R));
+        L.hrrpart = take((size_t)lbmk::hrr_blocks(c->N) * (1 + R));
+    }
+    if (nsteps > 0 && every > 0) {
         L.lamA = take(pop);
         L.lamB = take(pop);
         L.ck = take((size_t)L.nck * pop);
         L.ckT = take((size_t)L.nck * N);
         L.seg = take((size_t)every * pop);
         L.segT = take((size_t)every * N);
-        L.jpart = take((size_t)nsteps * (1 + R));
-        L.hrrpart = take((size_t)lbmk::hrr_blocks(c->N) * (1 + R));
         L.dT0 = take(N);
-    } else {
-        L.lamA = L.lamB = L.ck = L.ckT = L.seg = L.segT = L.jpart = L.hrrpart = L.dT0 = 0;
     }
     L.total = off * sizeof(double);
     return L;
@@ -775,7 +777,7 @@ int lbm_heat_release_adjoint(lbm_ctx *c, double *dJ_dF)
 
 int lbm_adjoint_workspace_bytes(const lbm_ctx *c, int nsteps, int every, size_t *bytes)
 {
-    if (!c || !bytes || nsteps < 0 || every < 1) return LBM_ERR_ARG;
+    if (!c || !bytes || nsteps < 0 || every < 0 || (every == 0 && nsteps == 0)) return LBM_ERR_ARG;
     *bytes = adj_layout(c, nsteps, every).total + 256;      // room to align the caller's base
     return LBM_OK;
 }
@@ -850,7 +852,8 @@ int lbm_heat_release_gradient(lbm_ctx *c, int nsteps, int every, double *J, doub
     if (od != LBM_OK) return od;
     const int sup = adjoint_supported(c);
     if (sup != LBM_OK) return sup;
-    const AdjLayout L = adj_layout(c, nsteps, every);
+    const bool grads = dJ_dlogA || dJ_dT0;
+    const AdjLayout L = adj_layout(c, nsteps, grads ? every : 0);
     if (workspace_bytes < L.total + 256 || !is_device_ptr(workspace)) return LBM_ERR_ARG;
     const bool T0_dev = dJ_dT0 && is_device_ptr(dJ_dT0);
     const size_t N = (size_t)c->N, pop = (size_t)c->S * LBMK_Q * N, popb = pop * sizeof(double);
@@ -864,9 +867,10 @@ int lbm_heat_release_gradient(lbm_ctx *c, int nsteps, int every, double *J, doub
     int st = LBM_OK;
 
     // Forward sweep: J_t at every step, the state and temperature row every
-    // checkpoint_every steps.
+    // checkpoint_every steps (no checkpoints and no reverse sweep when no
+    // gradient is asked for).
     for (int t = 0; t < nsteps && st == LBM_OK; ++t) {
-        if (t % every == 0) {
+        if (grads && t % every == 0) {
             const int k = t / every;
             st = copy_d2d(w + L.ck + (size_t)k * pop, c->buf[c->cur], popb, s);
             if (st == LBM_OK) st = copy_d2d(w + L.ckT + (size_t)k * N, Trow, Tb, s);
@@ -879,6 +883,18 @@ int lbm_heat_release_gradient(lbm_ctx *c, int nsteps, int every, double *J, doub
     if (st == LBM_OK) st = copy_d2d(w + L.tkeep, Trow, Tb, s);
     if (st == LBM_OK) st = lbm_sync(c);                  // a failed forward sweep stops here
     if (st != LBM_OK) return st;
+    if (!grads) {
+        double *hJ = (double *)malloc((size_t)nsteps * W * sizeof(double));
+        if (!hJ) return LBM_ERR_ARG;
+        st = check_cuda(cudaMemcpy(hJ, w + L.jpart, (size_t)nsteps * W * sizeof(double), cudaMemcpyDeviceToHost));
+        if (st == LBM_OK) {
+            double acc = 0.0;
+            for (int t = 0; t < nsteps; ++t) acc += hJ[(size_t)t * W];
+            *J = acc;
+        }
+        free(hJ);
+        return st;
+    }
 
     // Reverse sweep, segment by segment from the last.
     if (lbmk::adj_upload(c->slot, c->mc, s)) return LBM_ERR_CUDA;

@@ -522,6 +522,7 @@ class Solver:
         return out
 
     def _workspace(self, nsteps: int, every: int):
+        """A device workspace for the adjoint calls (see lbm_adjoint_workspace_bytes)."""
         nb = lbm_adjoint_workspace_bytes(self.ctx, nsteps, every)
         return self.torch.empty(nb, dtype=self.torch.uint8, device=self.device), nb
 
@@ -539,6 +540,15 @@ class Solver:
         _check(lbm_adjoint_step(self.ctx, lam_next.data_ptr(), lam.data_ptr(), dA, with_objective, ws.data_ptr(), nb),
                "lbm_adjoint_step")
         return lam, dA[:self.R]
+
+    @_on_device
+    def heat_release_total(self, steps: int):
+        """J alone: the forward sweep of lbm_heat_release_gradient."""
+        ws, nb = self._workspace(steps, 0)
+        J = np.zeros(1)
+        _check(lbm_heat_release_gradient(self.ctx, steps, steps, J, None, None, ws.data_ptr(), nb),
+               "lbm_heat_release_gradient")
+        return float(J[0])
 
     @_on_device
     def heat_release_gradient(self, steps: int, checkpoint_every: int = 64):
@@ -633,7 +643,7 @@ def _heat_release_function():
         @staticmethod
         def backward(ctx, gJ):
             dA, dT0 = ctx.saved_tensors
-            return gJ * dA, gJ * dT0, None, None, None
+            return gJ.to(dA.device) * dA, gJ.to(dT0.device) * dT0, None, None, None
 
     return HeatReleaseObjective
 
