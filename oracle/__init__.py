@@ -29,6 +29,8 @@ class OrcParams(C.Structure):
         ("r_lat", C.c_double), ("visc_model", C.c_int), ("R", C.c_int), ("nu_f", _ip), ("nu_r", _ip), ("log_A", _dp),
         ("b", _dp), ("theta", _dp), ("rtype", _ip), ("eff", _dp), ("low", _dp),
         ("reversible", _ip), ("T_ref", C.c_double), ("P0", C.c_double),
+        ("transport", C.c_int), ("mu0", _dp), ("mu_exp", _dp), ("T_tr", C.c_double), ("D_exp", C.c_double),
+        ("P_tr", C.c_double),
     ]
 
 
@@ -69,6 +71,7 @@ def _bind(L):
     L.orc_total_heat_release.argtypes = [C.c_void_p, _ip]
     L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
     L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
+    L.orc_transport.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
     L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
     L.orc_grad_pop.argtypes = [C.c_double, _dp, _dp, _dp]
     return L
@@ -132,7 +135,11 @@ class Oracle:
             R=mech.R, nu_f=i("nu_f", mech.nu_f), nu_r=i("nu_r", mech.nu_r),
             log_A=d("log_A", mech.log_A), b=d("b", mech.b), theta=d("theta", mech.theta),
             rtype=i("rtype", mech.rtype), eff=d("eff", mech.eff), low=d("low", mech.low),
-            reversible=i("reversible", mech.reversible), T_ref=mech.T_ref, P0=mech.P0)
+            reversible=i("reversible", mech.reversible), T_ref=mech.T_ref, P0=mech.P0,
+            transport=species.transport,
+            mu0=d("mu0", species.mu0) if species.mu0 is not None else None,
+            mu_exp=d("mu_exp", species.mu_exp) if species.mu_exp is not None else None,
+            T_tr=species.T_tr, D_exp=species.D_exp, P_tr=species.P_tr)
         self._h = self._L.orc_create(C.byref(p))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
@@ -220,6 +227,13 @@ class Oracle:
         J = float(self._L.orc_total_heat_release(self._h, C.byref(st)))
         assert st.value == 0, st.value
         return J
+
+    def transport(self, Y, T, P):
+        """dict nup (1/omega - 1/2), nup1 (1/omega_1 - 1/2), mu, lam, dfac at a node state."""
+        Y = np.ascontiguousarray(Y, dtype=np.float64)
+        out = np.zeros(5)
+        self._L.orc_transport(self._h, _d(Y), float(T), float(P), _d(out))
+        return dict(zip(("nup", "nup1", "mu", "lam", "dfac"), out.tolist()))
 
     def diffusion_velocities(self, Y, ua_minus_u, T):
         Y = np.ascontiguousarray(Y, dtype=np.float64)

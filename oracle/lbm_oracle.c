@@ -42,7 +42,8 @@
  *   - viscosity either from a constant kinematic viscosity (mu = rho nu, so
  *     1/omega = 1/2 + nu/(R T)) or a constant relaxation (1/omega - 1/2 =
  *     nu); conductivity from a constant Prandtl number, 1/omega_1 - 1/2 =
- *     (1/omega - 1/2)/Pr;
+ *     (1/omega - 1/2)/Pr; or mixture-averaged transport (mixture_transport:
+ *     seeded species power laws with the Wilke and Mathur mixing rules);
  *   - chemistry is a mass-action Arrhenius mechanism (third-body and
  *     Lindemann falloff forms, reverse rates from equilibrium constants of
  *     the species Gibbs energies) evaluated with concentrations rho_a/W_a;
@@ -88,6 +89,10 @@ typedef struct {
     const double *low;      /* [R][3] */
     const int *reversible;  /* [R] */
     double T_ref, P0;
+    int transport;          /* 0: constant nu, Pr, D_ab; 1: mixture-averaged (below) */
+    const double *mu0;      /* [M] species viscosity at T_tr (transport = 1) */
+    const double *mu_exp;   /* [M] its temperature exponent */
+    double T_tr, D_exp, P_tr;
 } orc_params;
 
 typedef struct {
@@ -105,6 +110,8 @@ typedef struct {
     double eff[ORC_MAXR][ORC_MAXM], low[ORC_MAXR][3];
     int reversible[ORC_MAXR];
     double T_ref, P0;
+    int transport;
+    double mu0[ORC_MAXM], mu_exp[ORC_MAXM], T_tr, D_exp, P_tr;
     /* state */
     double *pop;    /* [N][S][27] post-collision populations, stored at their node */
     double *tmp;    /* [N][S][27] populations after the pull */
@@ -326,10 +333,69 @@ static double nu_prime(const orc_state *s, double Rmix, double T)
     return s->visc_model == 0 ? s->nu / (Rmix * T) : s->nu;
 }
 
-/* 1/tau_ab = m R_U T / (m_a m_b D_ab), Eq. (tauab). */
+/* 1/tau_ab = m R_U T / (m_a m_b D_ab), Eq. (tauab); dfac scales every
+ * binary diffusivity (1 for constant transport). */
 static double inv_tau_ab(const orc_state *s, int a, int b, double m, double T)
 {
     return m * s->r_lat * T / (s->W[a] * s->W[b] * s->D[a][b]);
+}
+
+/* Mixture-averaged transport, the stand-in for the coefficients the paper
+ * takes from Cantera (Sec. 3, after Eq. (lambda)): species viscosities
+ * mu_a = mu0_a (T/T_tr)^{s_a}; Wilke's mixing rule (Wilke 1950)
+ *   mu = sum_a X_a mu_a / sum_b X_b Phi_ab,
+ *   Phi_ab = [1 + (mu_a/mu_b)^{1/2} (W_b/W_a)^{1/4}]^2 / [8 (1 + W_a/W_b)]^{1/2};
+ * species conductivities by the modified Eucken relation
+ * lambda_a = mu_a (C_p,a + 5/4 R_a); the average of Mathur, Tondon and
+ * Saxena (1967) lambda = (sum_a X_a lambda_a + 1 / sum_a X_a / lambda_a) / 2;
+ * binary diffusivities D_ab (T/T_tr)^{D_exp} (P_tr/P), so every 1/tau_ab
+ * is divided by dfac = (T/T_tr)^{D_exp} P_tr / P. */
+static void mixture_transport(const orc_state *s, const double *Y, double T, double P, double *mu, double *lambda,
+                              double *dfac)
+{
+    int M = s->M;
+    double X[ORC_MAXM], mua[ORC_MAXM], inv_m = 0.0;
+    for (int a = 0; a < M; ++a) inv_m += Y[a] / s->W[a];
+    for (int a = 0; a < M; ++a) {
+        X[a] = Y[a] / s->W[a] / inv_m;
+        mua[a] = s->mu0[a] * pow(T / s->T_tr, s->mu_exp[a]);
+    }
+    double num = 0.0, lsum = 0.0, lrec = 0.0;
+    for (int a = 0; a < M; ++a) {
+        double den = 0.0;
+        for (int b = 0; b < M; ++b) {
+            double r = 1.0 + sqrt(mua[a] / mua[b]) * pow(s->W[b] / s->W[a], 0.25);
+            den += X[b] * r * r / sqrt(8.0 * (1.0 + s->W[a] / s->W[b]));
+        }
+        num += X[a] * mua[a] / den;
+        double Ra = R_spec(s, a);
+        double lam_a = mua[a] * (Cv_spec(s, a, T) + Ra + 1.25 * Ra);
+        lsum += X[a] * lam_a;
+        lrec += X[a] / lam_a;
+    }
+    *mu = num;
+    *lambda = 0.5 * (lsum + 1.0 / lrec);
+    *dfac = pow(T / s->T_tr, s->D_exp) * s->P_tr / P;
+}
+
+/* Relaxation parameters: nup = 1/omega - 1/2 from Eq. (mu), mu = nup P dt;
+ * nup1 = 1/omega_1 - 1/2 from Eq. (lambda), lambda = nup1 P C_p dt; and the
+ * diffusivity factor dfac.  Constant transport: nup from nu_prime,
+ * nup1 = nup / Pr, dfac = 1. */
+static void relaxation(const orc_state *s, const double *Y, double Rmix, double T, double P, double *nup,
+                       double *nup1, double *dfac)
+{
+    if (!s->transport) {
+        *nup = nu_prime(s, Rmix, T);
+        *nup1 = *nup / s->Pr;
+        *dfac = 1.0;
+        return;
+    }
+    double mu, lambda, Cv = 0.0;
+    for (int a = 0; a < s->M; ++a) Cv += Y[a] * Cv_spec(s, a, T);
+    mixture_transport(s, Y, T, P, &mu, &lambda, dfac);
+    *nup = mu / P;
+    *nup1 = lambda / (P * (Cv + Rmix));
 }
 
 /* ------------------------------------------------------------------ */
@@ -367,6 +433,13 @@ orc_state *orc_create(const orc_params *p)
         for (int d = 0; d < 3; ++d) s->low[k][d] = p->low[3 * k + d];
     }
     s->T_ref = p->T_ref; s->P0 = p->P0;
+    s->transport = p->transport;
+    if (s->transport && (!p->mu0 || !p->mu_exp || !(p->T_tr > 0.0) || !(p->P_tr > 0.0))) return (free(s), NULL);
+    for (int a = 0; a < p->M; ++a) {
+        s->mu0[a] = p->mu0 ? p->mu0[a] : 0.0;
+        s->mu_exp[a] = p->mu_exp ? p->mu_exp[a] : 0.0;
+    }
+    s->T_tr = p->T_tr; s->D_exp = p->D_exp; s->P_tr = p->P_tr;
     size_t N = (size_t)s->N, S = (size_t)s->S, M = (size_t)s->M;
     s->pop = (double *)calloc(N * S * ORC_Q, sizeof(double));
     s->tmp = (double *)calloc(N * S * ORC_Q, sizeof(double));
@@ -599,7 +672,8 @@ static int moments_node(orc_state *s, size_t n)
     for (int a = 0; a < 3; ++a)
         s->Phi[n * 3 + a] = rho * u[a] * (1.0 - 3.0 * Rmix * T) - rho * u[a] * u[a] * u[a];
     /* Eq. (mu): 1/omega - 1/2 */
-    s->nup[n] = nu_prime(s, Rmix, T);
+    double nup1, dfac;
+    relaxation(s, s->Y + n * M, Rmix, T, rho * Rmix * T, &s->nup[n], &nup1, &dfac);
     return st;
 }
 
@@ -664,15 +738,17 @@ static int collide_node(orc_state *s, size_t n)
     double P = rho * Rmix * T;                                   /* Eq. (eosIdealGas) */
 
     /* relaxation parameters, Eqs. (mu) and (lambda) */
-    double omega = 1.0 / (0.5 + nu_prime(s, Rmix, T));
-    double omega1 = 1.0 / (0.5 + (1.0 / omega - 0.5) / s->Pr);
+    double nup, nup1, dfac;
+    relaxation(s, Y, Rmix, T, P, &nup, &nup1, &dfac);
+    double omega = 1.0 / (0.5 + nup);
+    double omega1 = 1.0 / (0.5 + nup1);
 
     /* Eq. (tauab) and Eq. (fStar): 1/tau_ab, 1/tau_a, beta_a */
     double itab[ORC_MAXM][ORC_MAXM], ita[ORC_MAXM], beta[ORC_MAXM];
     for (int a = 0; a < M; ++a) {
         ita[a] = 0.0;
         for (int b = 0; b < M; ++b) {
-            itab[a][b] = (a == b) ? 0.0 : inv_tau_ab(s, a, b, m, T);
+            itab[a][b] = (a == b) ? 0.0 : inv_tau_ab(s, a, b, m, T) / dfac;
             if (b != a) ita[a] += Y[b] * itab[a][b];
         }
         double tau_a = 1.0 / ita[a];
@@ -896,6 +972,18 @@ int orc_diffusion_velocities(const orc_state *s, const double *Y, const double *
     for (int a = 0; a < M; ++a)
         for (int d = 0; d < 3; ++d) du[3 * a + d] = x[a][d];
     return r;
+}
+
+/* Transport at a node state (Y [M], T, P): out = {1/omega - 1/2,
+ * 1/omega_1 - 1/2, mu, lambda, dfac} (mu and lambda zero for constant
+ * transport). */
+void orc_transport(const orc_state *s, const double *Y, double T, double P, double *out)
+{
+    double inv_m = 0.0;
+    for (int a = 0; a < s->M; ++a) inv_m += Y[a] / s->W[a];
+    relaxation(s, Y, s->r_lat * inv_m, T, P, &out[0], &out[1], &out[4]);
+    out[2] = out[3] = 0.0;
+    if (s->transport) mixture_transport(s, Y, T, P, &out[2], &out[3], &out[4]);
 }
 
 /* Equilibria of every set at a macroscopic state, layout [S][27]. */

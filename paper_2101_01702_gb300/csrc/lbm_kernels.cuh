@@ -411,9 +411,10 @@ __device__ __forceinline__ double poly5(const double u[6], double T)
 // Newton iteration on U(T) = e from T; stops when |dT| <= 1e-13 T.
 __device__ __forceinline__ double solve_T(const double u[6], double e, double T, unsigned *status)
 {
+    const double d5 = 5.0 * u[5], d4 = 4.0 * u[4], d3 = 3.0 * u[3], d2 = 2.0 * u[2];   // C_v's coefficients
     for (int it = 0; it < 50; ++it) {
         const double F = poly5(u, T) - e;
-        const double Fp = fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
+        const double Fp = fma(fma(fma(fma(d5, T, d4), T, d3), T, d2), T, u[1]);
         const double dT = F / Fp;
         T -= dT;
         if (!finite_bits(T)) { flag(status, LBMK_BIT_NONFINITE); return T; }
@@ -543,6 +544,56 @@ __device__ __forceinline__ bool node_of(Node &nd, const StepArgs &a)
     return true;
 }
 
+// Moments of one set from its 27 populations, row by row: the directions
+// come in 9 rows (cy, cz) of three (cx = -1, 0, 1); per row t = f- + f0 + f+
+// and dx = f+ - f-, so that
+//   sum f = sum t,  sum c_x f = sum dx,  sum c_y f = sum cy t,  sum c_z f = sum cz t,
+//   P_xx = sum (f- + f+), P_yy = sum_{cy != 0} t, P_zz = sum_{cz != 0} t,
+//   P_xy = sum cy dx, P_xz = sum cz dx, P_yz = sum cy cz t
+// (57 additions for the first four instead of 81 direction by direction).
+// ld(Dir<I>{}) returns the population of direction I.
+template <bool WITH_P, class V, class LD>
+__device__ __forceinline__ void row_moments(LD &&ld, V &s0, V &sx, V &sy, V &sz, V *P6)
+{
+    for_dirs<0, 9>([&](auto dj) {
+        constexpr int j = decltype(dj)::value, cy = j % 3 - 1, cz = j / 3 - 1;
+        const V fm = ld(Dir<3 * j>{}), f0 = ld(Dir<3 * j + 1>{}), fp = ld(Dir<3 * j + 2>{});
+        const V ac = fm + fp, t = ac + f0, dx = fp - fm;
+        if constexpr (j == 0) {                           // cy = cz = -1
+            s0 = t;
+            sx = dx;
+            sy = -t;
+            sz = -t;
+            if constexpr (WITH_P) {
+                P6[0] = ac;
+                P6[1] = t;
+                P6[2] = t;
+                P6[3] = -dx;
+                P6[4] = -dx;
+                P6[5] = t;
+            }
+        } else {
+            s0 += t;
+            sx += dx;
+            if constexpr (cy == 1) sy += t;
+            if constexpr (cy == -1) sy -= t;
+            if constexpr (cz == 1) sz += t;
+            if constexpr (cz == -1) sz -= t;
+            if constexpr (WITH_P) {
+                P6[0] += ac;
+                if constexpr (cy != 0) P6[1] += t;
+                if constexpr (cz != 0) P6[2] += t;
+                if constexpr (cy == 1) P6[3] += dx;
+                if constexpr (cy == -1) P6[3] -= dx;
+                if constexpr (cz == 1) P6[4] += dx;
+                if constexpr (cz == -1) P6[4] -= dx;
+                if constexpr (cy * cz == 1) P6[5] += t;
+                if constexpr (cy * cz == -1) P6[5] -= t;
+            }
+        }
+    });
+}
+
 // Moments of the pulled populations.  Species a < M-1 give rho_a and j_a;
 // f gives rho, j and (WITH_P) the pressure tensor; g gives rho E and q.
 struct Sums {
@@ -556,16 +607,12 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
     const PopView v = view(a.src, a);
 #pragma unroll
     for (int s = 0; s < M - 1; ++s) {
-        Real a0 = 0, ax = 0, ay = 0, az = 0;
-        for_dirs<0, LBMK_Q>([&](auto d) {
+        Real a0, ax, ay, az;
+        row_moments<false, Real>([&](auto d) {
             constexpr int I = decltype(d)::value;
-            if (LBMK_MIXED && I == REST) return;
-            const Real f = pull_sf(mc, v, a, s, I, p);
-            a0 += f;
-            if (CX(I)) ax += CX(I) * f;
-            if (CY(I)) ay += CY(I) * f;
-            if (CZ(I)) az += CZ(I) * f;
-        });
+            if (LBMK_MIXED && I == REST) return (Real)0;      // the double rest population: below
+            return pull_sf(mc, v, a, s, I, p);
+        }, a0, ax, ay, az, nullptr);
         rho_a[s] = (double)a0;
 #if LBMK_MIXED
         rho_a[s] += v.rest()[(size_t)s * a.N + n];
@@ -574,35 +621,20 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
         ja[s][1] = ay;
         ja[s][2] = az;
     }
-    Real a0 = 0, ax = 0, ay = 0, az = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-    double g0 = 0, qx = 0, qy = 0, qz = 0;
-    for_dirs<0, LBMK_Q>([&](auto d) {
+    double g0, qx, qy, qz;
+    row_moments<false, double>([&](auto d) { return pull_g(v, a, decltype(d)::value, p); }, g0, qx, qy, qz, nullptr);
+    Real a0, ax, ay, az, P6[6];
+    row_moments<WITH_P, Real>([&](auto d) {
         constexpr int I = decltype(d)::value;
-        const double g = pull_g(v, a, I, p);
-        g0 += g;
-        if (CX(I)) qx += CX(I) * g;
-        if (CY(I)) qy += CY(I) * g;
-        if (CZ(I)) qz += CZ(I) * g;
-        if (LBMK_MIXED && I == REST) return;
-        const Real f = pull_sf(mc, v, a, M - 1, I, p);
-        a0 += f;
-        if (CX(I)) ax += CX(I) * f;
-        if (CY(I)) ay += CY(I) * f;
-        if (CZ(I)) az += CZ(I) * f;
-        if constexpr (WITH_P) {
-            if (CX(I)) pxx += f;
-            if (CY(I)) pyy += f;
-            if (CZ(I)) pzz += f;
-            if (CX(I) && CY(I)) pxy += (CX(I) * CY(I)) * f;
-            if (CX(I) && CZ(I)) pxz += (CX(I) * CZ(I)) * f;
-            if (CY(I) && CZ(I)) pyz += (CY(I) * CZ(I)) * f;
-        }
-    });
+        if (LBMK_MIXED && I == REST) return (Real)0;
+        return pull_sf(mc, v, a, M - 1, I, p);
+    }, a0, ax, ay, az, P6);
     sm.rho = (double)a0;
     sm.rhoE = g0;
     sm.j[0] = ax; sm.j[1] = ay; sm.j[2] = az;
     sm.q[0] = qx; sm.q[1] = qy; sm.q[2] = qz;
-    sm.P[0] = pxx; sm.P[1] = pyy; sm.P[2] = pzz; sm.P[3] = pxy; sm.P[4] = pxz; sm.P[5] = pyz;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sm.P[k] = WITH_P ? (double)P6[k] : 0.0;
 #if LBMK_MIXED
     sm.rho += v.rest()[(size_t)(M - 1) * a.N + n];
 #endif
@@ -992,9 +1024,11 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     }
     const double Rm = mc.r_lat * inv_m;
     const double P = rho * Rm * T;
-    const double nup = nu_prime(mc, Rm, T);
-    const double omega = 1.0 / (0.5 + nup);
-    const double omega1 = 1.0 / (0.5 + nup / mc.Pr);
+    // relaxation rates (Eqs. (mu), (lambda)) in the storage type: in the
+    // mixed units they are stored and used as floats only
+    const Real nup = (Real)nu_prime(mc, Rm, T);
+    const Real omega = (Real)1 / ((Real)0.5 + nup);
+    const Real omega1 = (Real)1 / ((Real)0.5 + nup / (Real)mc.Pr);
 
     // enthalpies, Eq. (specHa)
     double Ha[M], H = 0.0;
@@ -1093,7 +1127,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     const double hk = H + 0.5 * usq;
     double qeq[3], Rt[6], tr3;
     energy_moments(rho, u, P, hk, sm.rhoE, qeq, Rt, tr3);
-    SReal dq[3];
+    Real dq[3], HaR[M], YR[M], duR[M][3];
     {
         const double dP[6] = {sm.P[0] - (P + rho * u[0] * u[0]), sm.P[1] - (P + rho * u[1] * u[1]),
                               sm.P[2] - (P + rho * u[2] * u[2]), sm.P[3] - rho * u[0] * u[1],
@@ -1101,16 +1135,25 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
         const double uP[3] = {u[0] * dP[0] + u[1] * dP[3] + u[2] * dP[4],
                               u[0] * dP[3] + u[1] * dP[1] + u[2] * dP[5],
                               u[0] * dP[4] + u[1] * dP[5] + u[2] * dP[2]};
-        SReal HY[M];
+        // Dq is stored in the storage type: the differences are formed in
+        // double (they cancel), the products with the stored values of
+        // omega, omega_1, H_a, Y_a and du_a in the storage type
+        Real HY[M];
 #pragma unroll
-        for (int s = 0; s < M; ++s) HY[s] = (SReal)Ha[s] * Yr[s];
-        const SReal orho = (SReal)(omega1 * rho);
+        for (int s = 0; s < M; ++s) {
+            HaR[s] = (Real)Ha[s];
+            YR[s] = (Real)Yr[s];
+            HY[s] = HaR[s] * YR[s];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) duR[s][d] = (Real)du[s][d];
+        }
+        const Real orho = omega1 * (Real)rho;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            SReal hyd = 0;
+            Real hyd = 0;
 #pragma unroll
-            for (int s = 0; s < M; ++s) hyd = fma(HY[s], du[s][d], hyd);
-            dq[d] = (SReal)((omega - omega1) * (sm.q[d] - uP[d] - qeq[d])) + orho * hyd;
+            for (int s = 0; s < M; ++s) hyd = fma(HY[s], duR[s][d], hyd);
+            dq[d] = (omega - omega1) * (Real)(sm.q[d] - uP[d] - qeq[d]) + orho * hyd;
         }
     }
 
@@ -1137,29 +1180,32 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     // storage-type rows
     const RecRows rr = rec_rows(M);
     Real *R = rec(a);
-    R[(size_t)rr.nup * N + n] = (Real)nup;
+    R[(size_t)rr.nup * N + n] = nup;
+    // Phi (Eq. (Xalpha)), stored in the storage type and formed in it
+    const Real rhoR = (Real)rho, rtR = (Real)(Rm * T), ph = (Real)1 - (Real)3 * rtR;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        R[(size_t)(rr.phi + d) * N + n] = (Real)(rho * u[d] * (1.0 - 3.0 * Rm * T) - rho * u[d] * u[d] * u[d]);
-        R[(size_t)(rr.u + d) * N + n] = (Real)ur[d];
-        R[(size_t)(rr.dq + d) * N + n] = (Real)dq[d];
+        const Real ud = (Real)ur[d];
+        R[(size_t)(rr.phi + d) * N + n] = rhoR * ud * (ph - ud * ud);
+        R[(size_t)(rr.u + d) * N + n] = ud;
+        R[(size_t)(rr.dq + d) * N + n] = dq[d];
     }
 #pragma unroll
     for (int s = 0; s < M; ++s) {
-        R[(size_t)(rr.y + s) * N + n] = (Real)Yr[s];
+        R[(size_t)(rr.y + s) * N + n] = YR[s];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = (Real)du[s][d];
+        for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = duR[s][d];
         // beta_a = 1/(2 tau_a + 1), Eq. (fStar): a parameter of the species
         // collision, formed in the storage type it is used in
         const Real it = (Real)ita[s];
         R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
-        R[(size_t)(rr.h + s) * N + n] = (Real)Ha[s];
+        R[(size_t)(rr.h + s) * N + n] = HaR[s];
     }
-    R[(size_t)rr.rho * N + n] = (Real)rho;
+    R[(size_t)rr.rho * N + n] = rhoR;
     R[(size_t)rr.kappa * N + n] = (Real)kap;
-    R[(size_t)rr.rt * N + n] = (Real)(Rm * T);
-    R[(size_t)rr.om * N + n] = (Real)omega;
-    R[(size_t)rr.om1 * N + n] = (Real)omega1;
+    R[(size_t)rr.rt * N + n] = rtR;
+    R[(size_t)rr.om * N + n] = omega;
+    R[(size_t)rr.om1 * N + n] = omega1;
     R[(size_t)rr.p * N + n] = (Real)P;
 }
 

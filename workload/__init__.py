@@ -20,4 +20,5 @@ from .configs import (  # noqa: F401
     mech9,
     mech3,
     node_states,
+    with_mixture_transport,
 )

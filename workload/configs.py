@@ -25,6 +25,7 @@ import math
 import numpy as np
 
 from .problem import (
+    TRANSPORT_MIXTURE_AVERAGED,
     BC_EQ_ZEROGRAD_U0LEFT,
     BC_PERIODIC,
     RXN_ELEMENTARY,
@@ -428,3 +429,29 @@ def node_states(M: int, n: int, seed: int = 2101, T_range=(700.0, 2600.0), rho_r
     Y = wts / wts.sum(axis=1, keepdims=True)
     rho_a = np.ascontiguousarray((Y * rho[:, None]).T)
     return rho_a, np.ascontiguousarray(T)
+
+
+def with_mixture_transport(species, X_ref, P_ref: float, T_ref: float, seed: int = 342,
+                           nup_ref: float = 0.45, D_exp: float = 1.5):
+    """A copy of species with seeded mixture-averaged transport (the stand-in
+    for the paper's Cantera transport): species viscosities
+    mu0_a = c sqrt(W_a) U[0.8, 1.2] at T_ref with exponents U[0.55, 0.65],
+    c set so that their mole-fraction average over X_ref equals
+    nup_ref * P_ref (so that 1/omega - 1/2 is near nup_ref in the reference
+    mixture); binary diffusivities D_ab (T/T_ref)^D_exp (P_ref/P) from the
+    species' constant D.  The exponents keep 1/omega - 1/2 within the
+    scheme's stable window (about 0.4 to 1.5) over 300-2000 K."""
+    import copy
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sp = copy.deepcopy(species)
+    W = np.asarray(sp.W, dtype=float)
+    raw = np.sqrt(W) * rng.uniform(0.8, 1.2, size=W.size)
+    X = np.asarray(X_ref, dtype=float)
+    X = X / X.sum()
+    sp.mu0 = raw * (nup_ref * P_ref / float(X @ raw))
+    sp.mu_exp = rng.uniform(0.55, 0.65, size=W.size)
+    sp.transport = TRANSPORT_MIXTURE_AVERAGED
+    sp.T_tr = float(T_ref)
+    sp.P_tr = float(P_ref)
+    sp.D_exp = float(D_exp)
+    return sp

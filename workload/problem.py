@@ -20,6 +20,9 @@ THERMO_POLY7 = 1
 VISC_KINEMATIC = 0
 VISC_RELAXATION = 1
 
+TRANSPORT_CONSTANT = 0
+TRANSPORT_MIXTURE_AVERAGED = 1
+
 RXN_ELEMENTARY = 0
 RXN_THIRD_BODY = 1
 RXN_FALLOFF = 2
@@ -54,6 +57,11 @@ class SpeciesSpec:
         mu = rho nu, so 1/omega - 1/2 = nu / (R T).
     visc_model == VISC_RELAXATION: nu is the constant 1/omega - 1/2, i.e.
         mu = nu P (a constant-relaxation-time gas).
+    transport == TRANSPORT_MIXTURE_AVERAGED replaces nu, Pr and the
+        constant D by mixture-averaged coefficients: species viscosities
+        mu0[a] (T/T_tr)^mu_exp[a], Wilke's rule for the mixture viscosity,
+        modified Eucken species conductivities with the Mathur-Tondon-Saxena
+        average, and binary diffusivities D[a][b] (T/T_tr)^D_exp (P_tr/P).
     """
     names: list
     W: np.ndarray          # [M] molar masses
@@ -69,6 +77,12 @@ class SpeciesSpec:
     elements: np.ndarray   # [E,M] element counts per species (test bookkeeping)
     element_names: list
     visc_model: int = 0
+    transport: int = 0
+    mu0: Optional[np.ndarray] = None      # [M]
+    mu_exp: Optional[np.ndarray] = None   # [M]
+    T_tr: float = 1.0
+    D_exp: float = 1.5
+    P_tr: float = 1.0
 
     @property
     def M(self) -> int:
