@@ -510,6 +510,30 @@ def run_ours(args):
         del sf
         torch.cuda.empty_cache()
 
+    # ---- mixture-averaged transport (viscosity, conductivity and
+    # diffusivities of each node's state) on the same lattice ---------------
+    transport = None
+    if not args.skip_fast and precision == lbm.LBM_MIXED:
+        pt = w.sphere3d_problem(n=n, radius=20.0 * n / 256.0)
+        pt.species = w.with_mixture_transport(pt.species, w.configs.PHI1_X + 1e-12, pt.mech.P0, 300.0)
+        st_ = lbm.Solver.from_problem(pt, precision=lbm.LBM_MIXED, stream=stream)
+        st_.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        pht = st_.step_timed(args.steps)
+        torch.cuda.synchronize()
+        barrier()
+        mst = float(pht[lbm.LBM_PHASES])
+        pht = pht[:lbm.LBM_PHASES] / args.steps
+        transport = {"mlups": N * args.steps * world / (mst * 1e-3) / 1e6, "steps": args.steps,
+                     "phase_ms": {"moments": pht[1], "gradients": pht[3], "energy_collision": pht[4],
+                                  "species_collision": pht[5]},
+                     "note": "LBM_MIXED with LBM_TRANSPORT_MIXTURE_AVERAGED (Wilke viscosity, Eucken/Mathur "
+                             "conductivity, power-law diffusivities per node)"}
+        st_.close()
+        del st_
+        torch.cuda.empty_cache()
+
     # ---- the double-precision step on the same lattice -------------------
     fp64 = None
     if not args.skip_fp64 and precision == lbm.LBM_MIXED:
@@ -555,6 +579,7 @@ def run_ours(args):
             "kernels": kernels,
             "autotuned_blocks": blocks,
             "mixed_fast_step": fast,
+            "mixture_averaged_transport_step": transport,
             "fp64_step": fp64,
             "heat_release": hrr,
             "adjoint": adjoint,

@@ -55,6 +55,7 @@ enum { LBM_BC_PERIODIC = 0, LBM_BC_EQ_ZEROGRAD_U0LEFT = 1 };
 enum { LBM_FP64 = 0, LBM_MIXED = 1, LBM_MIXED_FAST = 2 };
 enum { LBM_THERMO_CONST_CP = 0, LBM_THERMO_POLY7 = 1 };
 enum { LBM_VISC_KINEMATIC = 0, LBM_VISC_RELAXATION = 1 };
+enum { LBM_TRANSPORT_CONSTANT = 0, LBM_TRANSPORT_MIXTURE_AVERAGED = 1 };
 enum { LBM_RXN_ELEMENTARY = 0, LBM_RXN_THIRD_BODY = 1, LBM_RXN_FALLOFF = 2 };
 
 /* Lattice.  y and z are periodic.  bc_x = LBM_BC_PERIODIC wraps x;
@@ -109,7 +110,22 @@ typedef struct {
  *                LBM_VISC_RELAXATION: 1/omega - 1/2 = nu (mu = nu P).
  *   Pr           Prandtl number: 1/omega_1 - 1/2 = (1/omega - 1/2) / Pr (Eq. (lambda)).
  *   r_lat        universal gas constant in lattice units.
- * Unused arrays (cp_R/h_form for POLY7, poly7 for CONST_CP) may be NULL. */
+ *   transport    LBM_TRANSPORT_CONSTANT: nu, visc_model, Pr and D as above.
+ *                LBM_TRANSPORT_MIXTURE_AVERAGED: the viscosity, conductivity
+ *                and diffusivities of each node's state, the stand-in for
+ *                the coefficients the paper takes from Cantera (Sec. 3,
+ *                after Eq. (lambda)):
+ *                  mu_a = mu0[a] (T/T_tr)^mu_exp[a]  (species viscosities),
+ *                  mu by Wilke's mixing rule (Wilke 1950),
+ *                  lambda_a = mu_a (C_p,a + 5/4 R_a) (modified Eucken),
+ *                  lambda by the average of Mathur, Tondon and Saxena (1967),
+ *                  D_ab(T, P) = D[a][b] (T/T_tr)^D_exp (P_tr/P);
+ *                then 1/omega - 1/2 = mu / P (Eq. (mu)),
+ *                1/omega_1 - 1/2 = lambda / (P C_p) (Eq. (lambda)) and tau_ab
+ *                from D_ab(T, P) (Eq. (tauab)); nu and Pr are not used.
+ *                mu0, mu_exp [M]; T_tr, P_tr > 0.
+ * Unused arrays (cp_R/h_form for POLY7, poly7 for CONST_CP, mu0/mu_exp for
+ * constant transport) may be NULL. */
 typedef struct {
     int M;
     const double *W;
@@ -121,6 +137,10 @@ typedef struct {
     const double *D;
     double nu, Pr, r_lat;
     int visc_model;
+    int transport;
+    const double *mu0;
+    const double *mu_exp;
+    double T_tr, D_exp, P_tr;
 } lbm_species;
 
 /* Reaction mechanism giving the production rates rho_dot_a of Eq. (sumRhoDot)

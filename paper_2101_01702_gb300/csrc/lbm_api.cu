@@ -224,6 +224,7 @@ void references_from_stats(MechConst &mc, int M, const double *st, size_t N)
             const double v = r * psi_host(cx, zeta) * psi_host(cy, zeta) * psi_host(cz, zeta);
             mc.ref[s][i] = i == 13 ? 0.0f : (float)v;     // rest populations are stored in double
         }
+    lbmk_reference_moments(mc, M);
 }
 
 int check_cuda(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
@@ -274,10 +275,12 @@ AdjLayout adj_layout(const lbm_ctx *c, int nsteps, int every)
     return L;
 }
 
-// LBM_OK when the adjoint supports context c (double precision, one periodic lattice).
+// LBM_OK when the adjoint supports context c (double precision, one
+// periodic lattice, constant transport).
 int adjoint_supported(const lbm_ctx *c)
 {
-    if (c->lat.precision != LBM_FP64 || c->lat.bc_x != LBM_BC_PERIODIC || c->nseg > 1) return LBM_ERR_UNSUPPORTED;
+    if (c->lat.precision != LBM_FP64 || c->lat.bc_x != LBM_BC_PERIODIC || c->nseg > 1 || c->mc.transport)
+        return LBM_ERR_UNSUPPORTED;
     return LBM_OK;
 }
 
@@ -1038,6 +1041,7 @@ int lbm_set_references(lbm_ctx *c, const float *ref)
             if (!isfinite(ref[s * LBMK_Q + i])) return LBM_ERR_ARG;
             c->mc.ref[s][i] = i == 13 ? 0.0f : ref[s * LBMK_Q + i];   // rest populations are stored in double
         }
+    lbmk_reference_moments(c->mc, c->M);
     c->refs_fixed = true;
     return reslot(c);
 }

@@ -100,11 +100,40 @@ struct MechConst {
     double log_A[LBMK_MAXR], b[LBMK_MAXR], theta[LBMK_MAXR];
     double dlow[LBMK_MAXR][3];                              // falloff: ln(A0/A), b0 - b, theta0 - theta
     double eff[LBMK_MAXR][LBMK_MAXM];
+    // Mixture-averaged transport (transport = 1): species viscosity law,
+    // Wilke's mass factors wq[a][b] = (W_b/W_a)^(1/4) and
+    // wd[a][b] = (8 (1 + W_a/W_b))^(-1/2), 5/4 R_a for Eucken's relation, and
+    // the diffusivity law (T/T_tr)^D_exp (P_tr/P).
+    int transport;
+    double mu0[LBMK_MAXM], mu_exp[LBMK_MAXM], eucken[LBMK_MAXM];
+    double wq[LBMK_MAXM][LBMK_MAXM], wd[LBMK_MAXM][LBMK_MAXM];
+    double log_T_tr, D_exp, P_tr;
     // Mixed precision: stored float value = population - ref[s][i] for the
     // moving directions of the species and mixture sets (s < M); ref is a
     // rest state of set s (zero in the rest slot, which is not used).
     float ref[LBMK_MAXS][LBMK_Q];
+    // Moments of each set's rest state ref (exact sums in double): the
+    // zeroth moment and the diagonal of the second; the first moments and
+    // the off-diagonal second moments vanish by symmetry.  The mixed units
+    // sum the stored deviations and add these once.
+    double ref0[LBMK_MAXS], refP[LBMK_MAXS][3];
 };
+
+// Fills mc.ref0 and mc.refP from mc.ref (M species and mixture sets).
+inline void lbmk_reference_moments(MechConst &mc, int M)
+{
+    for (int s = 0; s < M; ++s) {
+        double z = 0.0, p[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < LBMK_Q; ++i) {
+            const double r = (double)mc.ref[s][i];
+            const int c[3] = {i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1};
+            z += r;
+            for (int d = 0; d < 3; ++d) p[d] += c[d] * c[d] * r;
+        }
+        mc.ref0[s] = z;
+        for (int d = 0; d < 3; ++d) mc.refP[s][d] = p[d];
+    }
+}
 
 #define LBMK_BLOCK 128      // default block; the block of k_pre and k_step is at most this
 #define LBMK_MAXBLOCK 256   // largest block of the kernels tuned up to it (k_grad, k_step_g; k_chem)

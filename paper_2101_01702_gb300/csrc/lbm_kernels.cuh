@@ -408,6 +408,11 @@ __device__ __forceinline__ double poly5(const double u[6], double T)
     return fma(fma(fma(fma(fma(u[5], T, u[4]), T, u[3]), T, u[2]), T, u[1]), T, u[0]);
 }
 
+__device__ __forceinline__ double dpoly5(const double u[6], double T)
+{
+    return fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
+}
+
 // Newton iteration on U(T) = e from T; stops when |dT| <= 1e-13 T.
 __device__ __forceinline__ double solve_T(const double u[6], double e, double T, unsigned *status)
 {
@@ -431,9 +436,60 @@ __device__ __forceinline__ double H_spec(const MechConst &mc, int a, double T)
     return fma(fma(fma(fma(fma(h[4], T, h[3]), T, h[2]), T, h[1]), T, h[0]), T, h[5]);
 }
 
+// Specific heat C_p,a(T) = dH_a/dT.
+__device__ __forceinline__ double cp_spec(const MechConst &mc, int a, double T)
+{
+    const double *h = mc.hco[a];
+    return fma(fma(fma(fma(5.0 * h[4], T, 4.0 * h[3]), T, 3.0 * h[2]), T, 2.0 * h[1]), T, h[0]);
+}
+
 __device__ __forceinline__ double nu_prime(const MechConst &mc, double Rm, double T)
 {
     return mc.visc_model == 0 ? mc.nu / (Rm * T) : mc.nu;
+}
+
+// Mixture-averaged transport of a node state (mc.transport = 1; Sec. 3
+// after Eq. (lambda), where the paper takes the coefficients from Cantera):
+// species viscosities mu_a = mu0_a (T/T_tr)^s_a, Wilke's mixing rule
+//   mu = sum_a X_a mu_a / sum_b X_b Phi_ab,
+//   Phi_ab = (1 + (mu_a/mu_b)^(1/2) (W_b/W_a)^(1/4))^2 / (8 (1 + W_a/W_b))^(1/2),
+// Eucken's lambda_a = mu_a (C_p,a + 5/4 R_a) with the average of Mathur,
+// Tondon and Saxena lambda = (sum X_a lambda_a + 1/sum X_a/lambda_a)/2;
+// returns 1/omega - 1/2 = mu/P (Eq. (mu)), 1/omega_1 - 1/2 = lambda/(P C_p)
+// (Eq. (lambda)) in the storage type, and the factor dfac =
+// (T/T_tr)^D_exp P_tr/P of every binary diffusivity (Eq. (tauab)).
+template <int M>
+__device__ void mixture_transport(const MechConst &mc, const double *Y, double inv_m, double T, double P,
+                                  double Cp, Real &nup, Real &nup1, double &dfac)
+{
+    const double lnT = log(T) - mc.log_T_tr;
+    const Real iim = (Real)(1.0 / inv_m);
+    Real X[M], mu[M], r[M], ir[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        X[a] = (Real)(Y[a] * mc.invW[a]) * iim;
+        mu[a] = (Real)mc.mu0[a] * exp((Real)(mc.mu_exp[a] * lnT));
+        r[a] = sqrt(mu[a]);
+        ir[a] = (Real)1 / r[a];
+    }
+    Real num = 0, ls = 0, lr = 0;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        Real den = 0;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const Real t = fma(r[a] * ir[b], (Real)mc.wq[a][b], (Real)1);
+            den = fma(X[b], t * t * (Real)mc.wd[a][b], den);
+        }
+        num += X[a] * mu[a] / den;
+        const Real lam = mu[a] * (Real)(cp_spec(mc, a, T) + mc.eucken[a]);
+        ls = fma(X[a], lam, ls);
+        lr += X[a] / lam;
+    }
+    const Real lambda = (Real)0.5 * (ls + (Real)1 / lr);
+    nup = num / (Real)P;
+    nup1 = lambda / (Real)(P * Cp);
+    dfac = exp(mc.D_exp * lnT) * mc.P_tr / P;
 }
 
 // Product-form factor Psi_c(xi, zeta) of Eq. (phis) with s = xi^2 + zeta.
@@ -600,6 +656,18 @@ struct Sums {
     double rho, j[3], P[6], rhoE, q[3];   // P: xx, yy, zz, xy, xz, yz
 };
 
+// In the mixed units the moving populations are summed as the stored float
+// deviations from the set's rest state; its moments (ref0, refP: double,
+// the first moments vanish) and the double rest population are added once.
+#if LBMK_MIXED
+__device__ __forceinline__ Real pull_dev(const MechConst &mc, const PopView &v, const StepArgs &a, int s, int i,
+                                         const PullIdx &p)
+{
+    const Src sr = src_of(i, p, a);
+    return sr.ghost ? (Real)load_ghost(a, sr.side, s, i, sr.idx) - RAWREF(s, i) : load_raw_sf(v, s, i, sr.idx);
+}
+#endif
+
 template <int M, bool WITH_P>
 __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs &a, const PullIdx &p, int n,
                                              double *rho_a, Real (*ja)[3], Sums &sm)
@@ -610,12 +678,16 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
         Real a0, ax, ay, az;
         row_moments<false, Real>([&](auto d) {
             constexpr int I = decltype(d)::value;
-            if (LBMK_MIXED && I == REST) return (Real)0;      // the double rest population: below
+#if LBMK_MIXED
+            if (I == REST) return (Real)0;                    // the double rest population: below
+            return pull_dev(mc, v, a, s, I, p);
+#else
             return pull_sf(mc, v, a, s, I, p);
+#endif
         }, a0, ax, ay, az, nullptr);
         rho_a[s] = (double)a0;
 #if LBMK_MIXED
-        rho_a[s] += v.rest()[(size_t)s * a.N + n];
+        rho_a[s] += mc.ref0[s] + v.rest()[(size_t)s * a.N + n];
 #endif
         ja[s][0] = ax;
         ja[s][1] = ay;
@@ -626,8 +698,12 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
     Real a0, ax, ay, az, P6[6];
     row_moments<WITH_P, Real>([&](auto d) {
         constexpr int I = decltype(d)::value;
-        if (LBMK_MIXED && I == REST) return (Real)0;
+#if LBMK_MIXED
+        if (I == REST) return (Real)0;
+        return pull_dev(mc, v, a, M - 1, I, p);
+#else
         return pull_sf(mc, v, a, M - 1, I, p);
+#endif
     }, a0, ax, ay, az, P6);
     sm.rho = (double)a0;
     sm.rhoE = g0;
@@ -636,7 +712,10 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
 #pragma unroll
     for (int k = 0; k < 6; ++k) sm.P[k] = WITH_P ? (double)P6[k] : 0.0;
 #if LBMK_MIXED
-    sm.rho += v.rest()[(size_t)(M - 1) * a.N + n];
+    sm.rho += mc.ref0[M - 1] + v.rest()[(size_t)(M - 1) * a.N + n];
+    if constexpr (WITH_P)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sm.P[d] += mc.refP[M - 1][d];
 #endif
 }
 
@@ -1016,19 +1095,28 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     // temperature, Eq. (temperature)
     const int n = nd.n;
     const size_t N = a.N;
-    double T;
+    double T, Cv = 0.0;
     {
         double eu[6];
         mixture_energy_poly<M>(mc, Y, eu);
         T = solve_T(eu, sm.rhoE * ir - 0.5 * usq, a.macro[DR_T * N + n], a.status);
+        if (mc.transport) Cv = dpoly5(eu, T);
     }
     const double Rm = mc.r_lat * inv_m;
     const double P = rho * Rm * T;
     // relaxation rates (Eqs. (mu), (lambda)) in the storage type: in the
-    // mixed units they are stored and used as floats only
-    const Real nup = (Real)nu_prime(mc, Rm, T);
+    // mixed units they are stored and used as floats only; dfac scales the
+    // binary diffusivities of mixture-averaged transport
+    Real nup, nup1;
+    double dfac = 1.0;
+    if (mc.transport) {
+        mixture_transport<M>(mc, Y, inv_m, T, P, Cv + Rm, nup, nup1, dfac);
+    } else {
+        nup = (Real)nu_prime(mc, Rm, T);
+        nup1 = nup / (Real)mc.Pr;
+    }
     const Real omega = (Real)1 / ((Real)0.5 + nup);
-    const Real omega1 = (Real)1 / ((Real)0.5 + nup / (Real)mc.Pr);
+    const Real omega1 = (Real)1 / ((Real)0.5 + nup1);
 
     // enthalpies, Eq. (specHa)
     double Ha[M], H = 0.0;
@@ -1043,7 +1131,7 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     // the arithmetic is in SReal: double, or float in the fast mixed unit
     // (the results are stored as floats there, and the solve below is well
     // conditioned: B is diagonally dominant after the symmetric scaling by Y).
-    const double kappa = mc.r_lat * T / inv_m;
+    const double kappa = mc.transport ? mc.r_lat * T / (inv_m * dfac) : mc.r_lat * T / inv_m;
     const SReal kap = (SReal)kappa, irr = (SReal)ir;
     SReal Yr[M], ur[3] = {(SReal)u[0], (SReal)u[1], (SReal)u[2]};
 #pragma unroll
@@ -1816,12 +1904,6 @@ int run_ref_stats(const StepArgs &a, const double *X, const double *T, double P,
 // blocks in a fixed order, so that the totals repeat from run to run.
 // ---------------------------------------------------------------------
 
-// Specific heat C_p,a(T) = dH_a/dT.
-__device__ __forceinline__ double cp_spec(const MechConst &mc, int a, double T)
-{
-    const double *h = mc.hco[a];
-    return fma(fma(fma(fma(5.0 * h[4], T, 4.0 * h[3]), T, 3.0 * h[2]), T, 2.0 * h[1]), T, h[0]);
-}
 
 // hdot^c at one node state (T, rho_a) and its derivatives: d/dT into *dT,
 // d/drho_a into drho[M], and d/d ln A_k added to dA[k * stride] (k < R).
@@ -2099,10 +2181,6 @@ int run_temperature_at(const StepArgs &a, int n, const double *Y, const double *
 // and dJ/dF_si(x) is the value of node x + c_i for its set (for f:
 // d/drho + c_i . d/dj).
 // ---------------------------------------------------------------------
-__device__ __forceinline__ double dpoly5(const double u[6], double T)
-{
-    return fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
-}
 
 // adj [M + 4][N]: d hdot/d rho_s (s < M-1), d/d rho, d/d j (3), d/d rho E.
 template <int M>

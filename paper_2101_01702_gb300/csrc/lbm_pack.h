@@ -20,6 +20,10 @@ static inline int lbm_pack_tables(const lbm_species *sp, const lbm_mechanism *me
     if (sp->thermo != LBM_THERMO_CONST_CP && sp->thermo != LBM_THERMO_POLY7) return LBM_ERR_ARG;
     if (sp->visc_model != LBM_VISC_KINEMATIC && sp->visc_model != LBM_VISC_RELAXATION) return LBM_ERR_ARG;
     if (!(sp->r_lat > 0) || !(sp->nu > 0) || !(sp->Pr > 0)) return LBM_ERR_ARG;
+    if (sp->transport != LBM_TRANSPORT_CONSTANT && sp->transport != LBM_TRANSPORT_MIXTURE_AVERAGED) return LBM_ERR_ARG;
+    if (sp->transport == LBM_TRANSPORT_MIXTURE_AVERAGED &&
+        (!sp->mu0 || !sp->mu_exp || !(sp->T_tr > 0) || !(sp->P_tr > 0) || !isfinite(sp->D_exp)))
+        return LBM_ERR_ARG;
     if (sp->thermo == LBM_THERMO_CONST_CP && !(sp->T0 > 0)) return LBM_ERR_ARG;
     if (mech->R < 0 || mech->R > LBMK_MAXR) return LBM_ERR_ARG;
     if (mech->R > 0 && (!mech->nu_f || !mech->nu_r || !mech->log_A || !mech->b || !mech->theta || !mech->rtype ||
@@ -65,6 +69,22 @@ static inline int lbm_pack_tables(const lbm_species *sp, const lbm_mechanism *me
             mc.inv_WWD[a][b] = 1.0 / (sp->W[a] * sp->W[b] * D);
             mc.inv_WWD_f[a][b] = (float)mc.inv_WWD[a][b];
         }
+    }
+    mc.transport = sp->transport;
+    if (sp->transport == LBM_TRANSPORT_MIXTURE_AVERAGED) {
+        for (int a = 0; a < M; ++a) {
+            if (!(sp->mu0[a] > 0) || !isfinite(sp->mu_exp[a])) return LBM_ERR_ARG;
+            mc.mu0[a] = sp->mu0[a];
+            mc.mu_exp[a] = sp->mu_exp[a];
+            mc.eucken[a] = 1.25 * mc.Ra[a];
+            for (int b = 0; b < M; ++b) {
+                mc.wq[a][b] = pow(sp->W[b] / sp->W[a], 0.25);
+                mc.wd[a][b] = 1.0 / sqrt(8.0 * (1.0 + sp->W[a] / sp->W[b]));
+            }
+        }
+        mc.log_T_tr = log(sp->T_tr);
+        mc.D_exp = sp->D_exp;
+        mc.P_tr = sp->P_tr;
     }
     mc.log_T_ref = mech->R > 0 ? log(mech->T_ref) : 0.0;
     bool need_P0 = false;

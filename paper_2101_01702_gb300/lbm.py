@@ -39,6 +39,7 @@ LBM_F_RHO_A, LBM_F_RHOU, LBM_F_RHOE, LBM_F_T, LBM_F_P, LBM_F_Y, LBM_F_J_A = 1, 2
 LBM_F_RHO_DOT = 128
 LBM_F_HRR = 256
 LBM_PHASES = 6
+LBM_TRANSPORT_CONSTANT, LBM_TRANSPORT_MIXTURE_AVERAGED = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -52,7 +53,8 @@ class lbm_lattice(C.Structure):
 class lbm_species(C.Structure):
     _fields_ = [("M", C.c_int), ("W", _dp), ("thermo", C.c_int), ("cp_R", _dp), ("h_form", _dp),
                 ("T0", C.c_double), ("poly7", _dp), ("D", _dp), ("nu", C.c_double), ("Pr", C.c_double),
-                ("r_lat", C.c_double), ("visc_model", C.c_int)]
+                ("r_lat", C.c_double), ("visc_model", C.c_int), ("transport", C.c_int), ("mu0", _dp),
+                ("mu_exp", _dp), ("T_tr", C.c_double), ("D_exp", C.c_double), ("P_tr", C.c_double)]
 
 
 class lbm_mechanism(C.Structure):
@@ -352,9 +354,13 @@ class Solver:
             self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision, len(seg), i(seg))
         else:
             self.lat = lbm_lattice(lattice.nx, lattice.ny, lattice.nz, lattice.bc_x, precision, 0, None)
+        tr = getattr(species, "transport", 0)
         self.sp = lbm_species(self.M, d(species.W), species.thermo, d(species.cp_R), d(species.h_form),
                               species.T0, d(species.poly7), d(species.D), species.nu, species.Pr,
-                              species.r_lat, species.visc_model)
+                              species.r_lat, species.visc_model, tr,
+                              d(species.mu0) if tr else None, d(species.mu_exp) if tr else None,
+                              getattr(species, "T_tr", 1.0), getattr(species, "D_exp", 1.5),
+                              getattr(species, "P_tr", 1.0))
         R = mech.R
         self.mech = lbm_mechanism(R, i(mech.nu_f.reshape(R, -1)) if R else None,
                                   i(mech.nu_r.reshape(R, -1)) if R else None,

@@ -194,6 +194,12 @@ def test_create_rejects_bad_species(lib):
     t = _Tables(lib)
     t.sp.thermo = 7
     _expect_rejected(lib, t)
+    t = _Tables(lib)
+    t.sp.transport = 1                                   # mixture-averaged transport without its tables
+    _expect_rejected(lib, t)
+    t = _Tables(lib)
+    t.sp.transport = 4                                   # unknown transport model
+    _expect_rejected(lib, t)
 
 
 def test_create_rejects_bad_mechanisms(lib):
