@@ -137,6 +137,45 @@ def adjoint_timing(lbm, torch, steps: int = 2000, every: int = 64, nx: int = 512
                     "to the 21 ln A_k and T(x, 0); FP64"}
 
 
+def circular_flame_run(lbm, torch, stream, precision, n: int = 512, steps: int = 2000, every: int = 250):
+    """The perturbed circular expanding flame of Sec. 5b (Eq. (cflamePerturbation),
+    R_ig = 48, A0 = 0.05, n0 = 4) on a periodic n x n x 1 box: every `every`
+    steps the mean radius of the T = 3 T_u isoline (Eq. (rmean)) and the
+    isoline means of S_a and of rho S_d / rho_u (Eq. (sd)), from
+    lbm_flame_speeds and lbm_isoline_means; the time of the diagnostics."""
+    import workload as w
+    prob = w.circular_flame_problem(n=n, R_ig=48.0, A0=0.05, n0=4)
+    s = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
+    c = (n - 1) / 2.0
+    T_u = 298.0
+    rec = []
+    t_diag = 0.0
+    t = 0
+    while True:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = s.moments(lbm.LBM_F_T | lbm.LBM_F_RHO_A, device=True)
+        Sd, Sa = s.flame_speeds(device=True)
+        rho = m["rho_a"].sum(dim=0)
+        rho_u = float(rho[0].item())                  # a corner node: unburnt
+        out = s.isoline_means(m["T"], 3 * T_u, c, c, [Sa, rho * Sd / rho_u])
+        torch.cuda.synchronize()
+        t_diag += time.perf_counter() - t0
+        rec.append({"step": t, "length": out[0], "R_mean": out[1], "S_a": out[2], "S_d_hat": out[3]})
+        del m, Sd, Sa, rho
+        if t >= steps:
+            break
+        s.step(every)
+        t += every
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": prob.name, "isoline": "T = 3 T_u", "samples": rec,
+            "diagnostics_ms": 1e3 * t_diag / len(rec),
+            "note": "lattice units; quasi-2D periodic box (the paper's quarter domain with symmetry and "
+                    "characteristic outlets is not built); burnt region of the unburnt composition at T_b"}
+
+
 def stored_bytes_per_node(M: int, mixed: bool) -> int:
     """Bytes of one copy of the stored state per node: in mixed precision the
     26 moving populations of the M species/mixture sets in float, their rest
@@ -551,6 +590,10 @@ def run_ours(args):
     if not args.skip_adjoint:
         adjoint = adjoint_timing(lbm, torch)
 
+    cflame = None
+    if not args.skip_cflame:
+        cflame = circular_flame_run(lbm, torch, stream, precision)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = _cpu_oracle_sample()
@@ -583,6 +626,7 @@ def run_ours(args):
             "fp64_step": fp64,
             "heat_release": hrr,
             "adjoint": adjoint,
+            "circular_flame": cflame,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -750,6 +794,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-hrr", action="store_true", help="skip the heat-release sensitivity measurement")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the gradients through time (512x4x4, 2000 steps)")
+    ap.add_argument("--skip-cflame", action="store_true", help="skip the perturbed circular flame (512x512x1)")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
     ap.add_argument("--cpu-legs", action="store_true",
                     help="instead of timing the GPU: the oracle's timed legs (64x4x4 200 steps, 32^3 1000 steps, "

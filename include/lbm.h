@@ -464,6 +464,35 @@ int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const 
  * the stream; LBM_ERR_ARG for NULL pointers or n < 0. */
 int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream);
 
+/* Flame diagnostics of the circular expanding flame (paper Sec. 5b) at the
+ * current state (the state the next collision sees): per node the local
+ * displacement speed of Eq. (sd),
+ *   S_d = [hdot^c + div(lambda grad T) - rho (sum_a C_a,p Y_a du_a) . grad T]
+ *         / (rho C_p |grad T|),
+ * with hdot^c = -sum_a H_a rho_dot_a, lambda = (1/omega_1 - 1/2) P C_p
+ * (Eq. (lambda)), the diffusion velocities du_a of Eq. (transform1) and the
+ * isotropic lattice gradients; and the absolute propagation speed
+ * S_a = S_d + u . n with n = -grad T / |grad T| (0 where grad T = 0).
+ *   Sd, Sa  host or device (both alike), double [N]
+ * The second population buffer serves as scratch; the state and the
+ * temperature row are unchanged.  Waits for the stream; returns like
+ * lbm_sync. */
+int lbm_flame_speeds(lbm_ctx *ctx, double *Sd, double *Sa);
+
+/* Means along the isoline T = T_iso in the plane z = 0, Eq. (rmean):
+ * A^{-1} int f dA over the isoline of length A, found by marching squares
+ * on the periodic x-y cells (crossings interpolated linearly along cell
+ * edges; a cell with four crossings split by the mean of its corners).
+ *   T        device, double [N]: the field whose isoline is taken
+ *   cx, cy   the centre for the distance R
+ *   fields   device, double [K][N] (K <= 8), or NULL for K = 0
+ *   out      host, double [2 + K]: {A, mean R, mean field_0 .. field_{K-1}}
+ * Positions are not wrapped: the isoline must not cross the box edge.
+ * Sums in a fixed order.  The second population buffer serves as scratch.
+ * Waits for the stream; LBM_ERR_ARG for NULL or host arrays, K > 8. */
+int lbm_isoline_means(lbm_ctx *ctx, const double *T, double T_iso, double cx, double cy, int K,
+                      const double *fields, double *out);
+
 /* Diagnostic (the paper has no counterpart): throughput of the GPU's
  * double-precision arithmetic, the peak the step's FP64-bound kernels are
  * measured against.  kind: LBM_PROBE_DFMA (independent fused multiply-add

@@ -72,6 +72,8 @@ def _bind(L):
     L.orc_diffusion_velocities.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
     L.orc_equilibrium_sets.argtypes = [C.c_void_p, _dp, _dp, C.c_double, _dp]
     L.orc_transport.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp]
+    L.orc_flame_speeds.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_isoline_means.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, C.c_double, C.c_int, _dp, _dp]
     L.orc_product_form.argtypes = [C.c_double, _dp, C.c_double, _dp]
     L.orc_grad_pop.argtypes = [C.c_double, _dp, _dp, _dp]
     return L
@@ -227,6 +229,23 @@ class Oracle:
         J = float(self._L.orc_total_heat_release(self._h, C.byref(st)))
         assert st.value == 0, st.value
         return J
+
+    def flame_speeds(self):
+        """S_d (Eq. (sd)) and S_a = S_d + u.n at every node of the current time level."""
+        Sd, Sa = np.empty(self.N), np.empty(self.N)
+        st = self._L.orc_flame_speeds(self._h, _d(Sd), _d(Sa))
+        assert st == 0, st
+        return Sd, Sa
+
+    def isoline_means(self, T, T_iso, cx, cy, fields=()):
+        """{A, R, means of fields} along T = T_iso in the plane z = 0 (Eq. (rmean))."""
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        K = len(fields)
+        assert K <= 16
+        F = np.ascontiguousarray(np.stack(fields) if K else np.zeros((1, self.N)), dtype=np.float64)
+        out = np.zeros(2 + K)
+        self._L.orc_isoline_means(self._h, _d(T), float(T_iso), float(cx), float(cy), K, _d(F), _d(out))
+        return out
 
     def transport(self, Y, T, P):
         """dict nup (1/omega - 1/2), nup1 (1/omega_1 - 1/2), mu, lam, dfac at a node state."""

@@ -974,6 +974,165 @@ int orc_diffusion_velocities(const orc_state *s, const double *Y, const double *
     return r;
 }
 
+/* ------------------------------------------------------------------ */
+/* Flame diagnostics of the circular expanding flame (Sec. 5b)         */
+/* ------------------------------------------------------------------ */
+/* Diffusion velocities du[M][3] of node n of the current time level
+ * (Eq. (transform1) with the relaxation of this node, as in collide_node). */
+static int node_diffusion_velocities(const orc_state *s, size_t n, double du[ORC_MAXM][3])
+{
+    int M = s->M;
+    double rho = s->rho[n], T = s->T[n];
+    const double *Y = s->Y + n * M, *rho_a = s->rho_a + n * M;
+    double u[3] = {s->j[n * 3] / rho, s->j[n * 3 + 1] / rho, s->j[n * 3 + 2] / rho};
+    double inv_m = 0.0;
+    for (int a = 0; a < M; ++a) inv_m += Y[a] / s->W[a];
+    double m = 1.0 / inv_m, Rmix = s->r_lat * inv_m, P = rho * Rmix * T;
+    double nup, nup1, dfac;
+    relaxation(s, Y, Rmix, T, P, &nup, &nup1, &dfac);
+    double A[ORC_MAXM][ORC_MAXM], rhs[ORC_MAXM][3];
+    for (int a = 0; a < M; ++a) {
+        double ita = 0.0;
+        for (int b = 0; b < M; ++b) if (b != a) ita += Y[b] * inv_tau_ab(s, a, b, m, T) / dfac;
+        for (int b = 0; b < M; ++b)
+            A[a][b] = (a == b) ? 1.0 + ita / 2.0 : -0.5 * inv_tau_ab(s, a, b, m, T) / dfac * Y[b];
+        for (int d = 0; d < 3; ++d) rhs[a][d] = s->j_a[(n * M + a) * 3 + d] / rho_a[a] - u[d];
+    }
+    return solve_linear(M, A, rhs, du);
+}
+
+/* The local displacement speed of Eq. (sd) and the absolute propagation
+ * speed at every node of the current time level:
+ *   S_d = [ -sum_a H_a rho_dot_a + div(lambda grad T)
+ *           - rho (sum_a C_a,p Y_a du_a) . grad T ] / (rho C_p |grad T|),
+ *   S_a = S_d + u . n,  n = -grad T / |grad T|,
+ * lambda = (1/omega_1 - 1/2) P C_p (Eq. (lambda)), the gradients by the
+ * isotropic lattice stencil (the divergence as the sum of the component
+ * derivatives of lambda grad T).  Nodes with grad T = 0 get 0. */
+int orc_flame_speeds(orc_state *s, double *Sd, double *Sa)
+{
+    int st = stream_and_moments(s);
+    int M = s->M;
+    size_t N = (size_t)s->N;
+    double *gT = (double *)calloc(3 * N, sizeof(double)), *lg = (double *)calloc(3 * N, sizeof(double));
+    double *Cp = (double *)calloc(N, sizeof(double));
+    if (!gT || !lg || !Cp) { free(gT); free(lg); free(Cp); return ORC_ERR_ARG; }
+    for (size_t n = 0; n < N; ++n) {
+        int x = (int)(n % s->nx), y = (int)((n / s->nx) % s->ny), z = (int)(n / ((size_t)s->nx * s->ny));
+        for (int i = 0; i < ORC_Q; ++i) {
+            size_t nb = stencil_neighbor(s, x, y, z, i);
+            int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+            for (int a = 0; a < 3; ++a) gT[n * 3 + a] += w_of(i) * c[a] * s->T[nb] / THETA;
+        }
+        const double *Y = s->Y + n * M;
+        double inv_m = 0.0, Cv = 0.0;
+        for (int a = 0; a < M; ++a) { inv_m += Y[a] / s->W[a]; Cv += Y[a] * Cv_spec(s, a, s->T[n]); }
+        double Rmix = s->r_lat * inv_m, P = s->rho[n] * Rmix * s->T[n];
+        double nup, nup1, dfac;
+        relaxation(s, Y, Rmix, s->T[n], P, &nup, &nup1, &dfac);
+        Cp[n] = Cv + Rmix;
+        double lam = nup1 * P * Cp[n];
+        for (int a = 0; a < 3; ++a) lg[n * 3 + a] = lam * gT[n * 3 + a];
+    }
+    for (size_t n = 0; n < N; ++n) {
+        int x = (int)(n % s->nx), y = (int)((n / s->nx) % s->ny), z = (int)(n / ((size_t)s->nx * s->ny));
+        double div = 0.0;
+        for (int i = 0; i < ORC_Q; ++i) {
+            size_t nb = stencil_neighbor(s, x, y, z, i);
+            int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+            for (int a = 0; a < 3; ++a) div += w_of(i) * c[a] * lg[nb * 3 + a] / THETA;
+        }
+        double T = s->T[n], rho = s->rho[n];
+        const double *Y = s->Y + n * M;
+        double wdot[ORC_MAXM], du[ORC_MAXM][3];
+        production_rates(s, s->rho_a + n * M, T, wdot);
+        int r = node_diffusion_velocities(s, n, du);
+        if (r != ORC_OK && st == ORC_OK) st = r;
+        double hdot = 0.0, fl[3] = {0, 0, 0};
+        for (int a = 0; a < M; ++a) {
+            hdot -= H_spec(s, a, T) * wdot[a];
+            double cpa = Cv_spec(s, a, T) + R_spec(s, a);
+            for (int d = 0; d < 3; ++d) fl[d] += cpa * Y[a] * du[a][d];
+        }
+        const double *g = gT + n * 3;
+        double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        if (gn == 0.0) { Sd[n] = Sa[n] = 0.0; continue; }
+        double num = hdot + div - rho * (fl[0] * g[0] + fl[1] * g[1] + fl[2] * g[2]);
+        Sd[n] = num / (rho * Cp[n] * gn);
+        double un = -(s->j[n * 3] * g[0] + s->j[n * 3 + 1] * g[1] + s->j[n * 3 + 2] * g[2]) / (rho * gn);
+        Sa[n] = Sd[n] + un;
+    }
+    free(gT); free(lg); free(Cp);
+    return st;
+}
+
+/* Means along the isoline T = T_iso in the plane z = 0, Eq. (rmean):
+ * A^{-1} \int f dA with A the isoline's length.  Marching squares on the
+ * cells (x, y)..(x+1, y+1) of the periodic x-y lattice: a crossing on a
+ * cell edge where T - T_iso changes sign (T >= T_iso counts as above), at
+ * the linear interpolation point, with the fields interpolated alike; the
+ * two crossings of a cell make one straight segment; a cell with four
+ * crossings is split according to the mean of its corners.  Each segment
+ * adds its length times the mean of its ends' values (the trapezoid rule).
+ * T [N], fields [K][N]; out = {A, mean R, mean field_0 .. field_{K-1}},
+ * R the distance from (cx, cy); positions are not wrapped (the isoline is
+ * assumed not to cross the box edge). */
+void orc_isoline_means(const orc_state *s, const double *T, double T_iso, double cx, double cy, int K,
+                       const double *fields, double *out)
+{
+    size_t N = (size_t)s->N;
+    int nx = s->nx, ny = s->ny;
+    double acc[2 + 16] = {0};
+    for (int k = 0; k < 2 + K; ++k) acc[k] = 0.0;
+    static const int ox[4] = {0, 1, 1, 0}, oy[4] = {0, 0, 1, 1};
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            size_t idx[4];
+            double v[4];
+            for (int c = 0; c < 4; ++c) {
+                idx[c] = (size_t)((x + ox[c]) % nx) + (size_t)nx * ((y + oy[c]) % ny);
+                v[c] = T[idx[c]];
+            }
+            double px[4], py[4], pf[4][16];
+            int ne = 0, edge[4];
+            for (int e = 0; e < 4; ++e) {
+                int a = e, b = (e + 1) % 4;
+                if ((v[a] >= T_iso) == (v[b] >= T_iso)) continue;
+                double t = (T_iso - v[a]) / (v[b] - v[a]);
+                px[ne] = x + ox[a] + t * (ox[b] - ox[a]);
+                py[ne] = y + oy[a] + t * (oy[b] - oy[a]);
+                for (int k = 0; k < K; ++k)
+                    pf[ne][k] = fields[(size_t)k * N + idx[a]] + t * (fields[(size_t)k * N + idx[b]] - fields[(size_t)k * N + idx[a]]);
+                edge[ne++] = e;
+            }
+            int pairs[2][2], np = 0;
+            if (ne == 2) { pairs[0][0] = 0; pairs[0][1] = 1; np = 1; }
+            else if (ne == 4) {
+                double vc = 0.25 * (v[0] + v[1] + v[2] + v[3]);
+                /* crossings are on edges 0, 1, 2, 3 in order; corner c lies
+                 * between edges c-1 and c */
+                if ((vc >= T_iso) == (v[0] >= T_iso)) {      /* corners 1 and 3 cut off */
+                    pairs[0][0] = 0; pairs[0][1] = 1; pairs[1][0] = 2; pairs[1][1] = 3;
+                } else {                                      /* corners 0 and 2 cut off */
+                    pairs[0][0] = 3; pairs[0][1] = 0; pairs[1][0] = 1; pairs[1][1] = 2;
+                }
+                np = 2;
+            }
+            (void)edge;
+            for (int q = 0; q < np; ++q) {
+                int i = pairs[q][0], j = pairs[q][1];
+                double L = sqrt((px[i] - px[j]) * (px[i] - px[j]) + (py[i] - py[j]) * (py[i] - py[j]));
+                double Ri = sqrt((px[i] - cx) * (px[i] - cx) + (py[i] - cy) * (py[i] - cy));
+                double Rj = sqrt((px[j] - cx) * (px[j] - cx) + (py[j] - cy) * (py[j] - cy));
+                acc[0] += L;
+                acc[1] += L * 0.5 * (Ri + Rj);
+                for (int k = 0; k < K; ++k) acc[2 + k] += L * 0.5 * (pf[i][k] + pf[j][k]);
+            }
+        }
+    out[0] = acc[0];
+    for (int k = 1; k < 2 + K; ++k) out[k] = acc[0] > 0.0 ? acc[k] / acc[0] : 0.0;
+}
+
 /* Transport at a node state (Y [M], T, P): out = {1/omega - 1/2,
  * 1/omega_1 - 1/2, mu, lambda, dfac} (mu and lambda zero for constant
  * transport). */

@@ -102,4 +102,21 @@ int hrr_adj_gather_fp64(const StepArgs &a, const double *adj, int s, double *out
 #undef CALL
 }
 
+int flame_fp64(const StepArgs &a, double *scratch, double *Sd, double *Sa)
+{
+#define CALL(M_) run_flame_speeds<M_>(a, scratch, Sd, Sa)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
+int isoline_fp64(int nx, int ny, int N, const double *T, double T_iso, double cx, double cy, int K,
+                 const double *fields, double *partial, double *out, cudaStream_t s)
+{
+    if (K < 0 || K > LBMK_ISO_MAXK) return (int)cudaErrorInvalidValue;
+    const int nb = isoline_blocks((long long)nx * ny);
+    k_isoline<<<nb, LBMK_HRR_THREADS, 0, s>>>(nx, ny, N, T, T_iso, cx, cy, K, fields, partial);
+    k_hrr_final<<<2 + K, LBMK_HRR_THREADS, 0, s>>>(partial, nb, 2 + K, out);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -81,4 +81,11 @@ int hrr_adj_gather_mixed(const StepArgs &a, const double *adj, int s, double *ou
 #undef CALL
 }
 
+int flame_mixed(const StepArgs &a, double *scratch, double *Sd, double *Sa)
+{
+#define CALL(M_) run_flame_speeds<M_>(a, scratch, Sd, Sa)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 }  // namespace lbmk

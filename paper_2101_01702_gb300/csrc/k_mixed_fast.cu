@@ -82,4 +82,11 @@ int hrr_adj_gather_mixed_fast(const StepArgs &a, const double *adj, int s, doubl
 #undef CALL
 }
 
+int flame_mixed_fast(const StepArgs &a, double *scratch, double *Sd, double *Sa)
+{
+#define CALL(M_) run_flame_speeds<M_>(a, scratch, Sd, Sa)
+    LBMK_DISPATCH(a.M, CALL)
+#undef CALL
+}
+
 }  // namespace lbmk

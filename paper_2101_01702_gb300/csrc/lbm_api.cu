@@ -65,15 +65,15 @@ const lbmk::PrecisionOps kOps[3] = {
     {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64,
      lbmk::launch_one_fp64, lbmk::hrr_fp64,
      lbmk::chem_at_fp64, lbmk::temperature_at_fp64,
-     lbmk::hrr_adj_fp64, lbmk::hrr_adj_gather_fp64},
+     lbmk::hrr_adj_fp64, lbmk::hrr_adj_gather_fp64, lbmk::flame_fp64},
     {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed,
      lbmk::launch_one_mixed, lbmk::hrr_mixed,
      lbmk::chem_at_mixed, lbmk::temperature_at_mixed,
-     lbmk::hrr_adj_mixed, lbmk::hrr_adj_gather_mixed},
+     lbmk::hrr_adj_mixed, lbmk::hrr_adj_gather_mixed, lbmk::flame_mixed},
     {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
      lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast, lbmk::hrr_mixed_fast,
      lbmk::chem_at_mixed_fast, lbmk::temperature_at_mixed_fast,
-     lbmk::hrr_adj_mixed_fast, lbmk::hrr_adj_gather_mixed_fast},
+     lbmk::hrr_adj_mixed_fast, lbmk::hrr_adj_gather_mixed_fast, lbmk::flame_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -960,6 +960,56 @@ int lbm_heat_release_gradient(lbm_ctx *c, int nsteps, int every, double *J, doub
     }
     free(hJ);
     return st;
+}
+
+int lbm_flame_speeds(lbm_ctx *c, double *Sd, double *Sa)
+{
+    if (!c || !Sd || !Sa || Sd == Sa) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    const size_t N = (size_t)c->N;
+    const bool dev = is_device_ptr(Sd);
+    if (dev != is_device_ptr(Sa)) return LBM_ERR_ARG;                // both host or both device
+    // scratch in the free population buffer: the kept temperature row, the
+    // gradients, then (host outputs) the two rows
+    double *stage = (double *)c->buf[1 - c->cur];
+    double *tkeep = stage, *scr = stage + N, *dSd = dev ? Sd : stage + 7 * N, *dSa = dev ? Sa : stage + 8 * N;
+    if ((dev ? 7 : 9) * N * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+    double *Trow = c->macro + (size_t)DR_T * N;
+    // the record pass overwrites the temperature row (the Newton starting
+    // point of the next step): kept aside and put back
+    int st = copy_d2d(tkeep, Trow, N * sizeof(double), c->stream);
+    if (st != LBM_OK) return st;
+    if (ops(c->lat.precision).flame(args_of(c), scr, dSd, dSa)) return LBM_ERR_CUDA;
+    if (!dev) {
+        st = check_cuda(cudaMemcpyAsync(Sd, dSd, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (st == LBM_OK) st = check_cuda(cudaMemcpyAsync(Sa, dSa, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (st != LBM_OK) return st;
+    }
+    st = copy_d2d(Trow, tkeep, N * sizeof(double), c->stream);
+    if (st != LBM_OK) return st;
+    return lbm_sync(c);
+}
+
+int lbm_isoline_means(lbm_ctx *c, const double *T, double T_iso, double cx, double cy, int K, const double *fields,
+                      double *out)
+{
+    if (!c || !T || !out || K < 0 || K > 8 || (K > 0 && !fields) || !isfinite(T_iso)) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    if (!is_device_ptr(T) || (K > 0 && !is_device_ptr(fields))) return LBM_ERR_ARG;
+    const int nb = lbmk::isoline_blocks((long long)c->lat.nx * c->lat.ny);
+    double *partial = (double *)c->buf[1 - c->cur], *dout = partial + (size_t)nb * (2 + K);
+    if (((size_t)nb * (2 + K) + 2 + K) * sizeof(double) > c->pop_bytes) return LBM_ERR_ARG;
+    if (lbmk::isoline_fp64(c->lat.nx, c->lat.ny, c->N, T, T_iso, cx, cy, K, fields, partial, dout, c->stream))
+        return LBM_ERR_CUDA;
+    double h[2 + 8];
+    int st = check_cuda(cudaMemcpyAsync(h, dout, (2 + K) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (st == LBM_OK) st = lbm_sync(c);
+    if (st != LBM_OK) return st;
+    out[0] = h[0];
+    for (int k = 1; k < 2 + K; ++k) out[k] = h[0] > 0.0 ? h[k] / h[0] : 0.0;
+    return LBM_OK;
 }
 
 int lbm_chemistry_at(lbm_ctx *c, int n, const double *rho_a, const double *T, double *rho_dot, double *hdot,

@@ -229,6 +229,18 @@ int hrr_adj_gather_fp64(const StepArgs &a, const double *adj, int s, double *out
 int hrr_adj_gather_mixed(const StepArgs &a, const double *adj, int s, double *out);
 int hrr_adj_gather_mixed_fast(const StepArgs &a, const double *adj, int s, double *out);
 
+// flame diagnostics of the state in src (lbm_flame_speeds): the record
+// pass, then S_d and S_a [N] (device); scratch holds 6 N doubles
+int flame_fp64(const StepArgs &a, double *scratch, double *Sd, double *Sa);
+int flame_mixed(const StepArgs &a, double *scratch, double *Sd, double *Sa);
+int flame_mixed_fast(const StepArgs &a, double *scratch, double *Sd, double *Sa);
+// isoline means in the plane z = 0 (lbm_isoline_means): T [N] and fields
+// [K][N] (device, K <= 8), partial isoline_blocks(nx ny) (2 + K) doubles of
+// scratch, out 2 + K doubles (device) {length, sum L R, sum L f_k}
+inline int isoline_blocks(long long cells) { return (int)((cells + LBMK_HRR_THREADS - 1) / LBMK_HRR_THREADS); }
+int isoline_fp64(int nx, int ny, int N, const double *T, double T_iso, double cx, double cy, int K,
+                 const double *fields, double *partial, double *out, cudaStream_t s);
+
 // one kernel of the step (LBMK_K_*) with the block size a.bs[kernel]
 int launch_one_fp64(const StepArgs &a, int kernel);
 int launch_one_mixed(const StepArgs &a, int kernel);
@@ -248,6 +260,7 @@ struct PrecisionOps {
     int (*temperature_at)(const StepArgs &a, int n, const double *Y, const double *e, const double *T0, double *T);
     int (*hrr_adj)(const StepArgs &a, double *adj);
     int (*hrr_adj_gather)(const StepArgs &a, const double *adj, int s, double *out);
+    int (*flame)(const StepArgs &a, double *scratch, double *Sd, double *Sa);
 };
 }  // namespace lbmk
 

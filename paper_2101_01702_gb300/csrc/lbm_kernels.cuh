@@ -2272,6 +2272,188 @@ int run_hrr_adj_gather(const StepArgs &a, const double *adj, int s, double *out)
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------
+// Flame diagnostics of the circular expanding flame (Sec. 5b), from the
+// record k_pre forms for the current state:
+//   S_d = [ hdot^c + div(lambda grad T) - rho (sum_a C_a,p Y_a du_a) . grad T ]
+//         / (rho C_p |grad T|)                                   (Eq. (sd))
+//   S_a = S_d + u . n,  n = -grad T / |grad T|,
+// lambda = (1/omega_1 - 1/2) P C_p (Eq. (lambda)), C_p = sum_a Y_a C_a,p,
+// the gradients by the isotropic stencil (the divergence as the sum of the
+// component derivatives of lambda grad T).  Pass 1 forms grad T and
+// lambda grad T (scratch [6][N]); pass 2 the rest.  S_d = S_a = 0 where
+// grad T = 0.
+// ---------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_flame1(StepArgs a, double *scr)
+{
+    const MechConst &mc = c_mech[a.slot];
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const size_t N = a.N;
+    const int n = nd.n;
+    const RecRows rr = rec_rows(M);
+    const Real *R = rec(a);
+    const double *Tr = a.macro + (size_t)DR_T * N;
+    StencilIdx st;
+    make_stencil(st, nd, a);
+    double g[3] = {0.0, 0.0, 0.0};
+    for_dirs<0, LBMK_Q>([&](auto dd) {
+        constexpr int I = decltype(dd)::value;
+        if constexpr (I != REST) {
+            const double t = Tr[nb_of<I>(st, a)];
+            if (CX(I)) g[0] = fma(WI(I) * CX(I), t, g[0]);
+            if (CY(I)) g[1] = fma(WI(I) * CY(I), t, g[1]);
+            if (CZ(I)) g[2] = fma(WI(I) * CZ(I), t, g[2]);
+        }
+    });
+    const double T = Tr[n];
+    double Cp = 0.0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) Cp = fma((double)R[(size_t)(rr.y + s) * N + n], cp_spec(mc, s, T), Cp);
+    const double lam = (1.0 / (double)R[(size_t)rr.om1 * N + n] - 0.5) * (double)R[(size_t)rr.p * N + n] * Cp;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        scr[(size_t)d * N + n] = 3.0 * g[d];
+        scr[(size_t)(3 + d) * N + n] = lam * 3.0 * g[d];
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_HRR_THREADS) k_flame2(StepArgs a, const double *scr, double *Sd, double *Sa)
+{
+    const MechConst &mc = c_mech[a.slot];
+    Node nd;
+    if (!node_of(nd, a)) return;
+    const size_t N = a.N;
+    const int n = nd.n;
+    const RecRows rr = rec_rows(M);
+    const Real *R = rec(a);
+    StencilIdx st;
+    make_stencil(st, nd, a);
+    double div = 0.0;
+    for_dirs<0, LBMK_Q>([&](auto dd) {
+        constexpr int I = decltype(dd)::value;
+        if constexpr (I != REST) {
+            const size_t nb = nb_of<I>(st, a);
+            if (CX(I)) div = fma(WI(I) * CX(I), scr[(size_t)3 * N + nb], div);
+            if (CY(I)) div = fma(WI(I) * CY(I), scr[(size_t)4 * N + nb], div);
+            if (CZ(I)) div = fma(WI(I) * CZ(I), scr[(size_t)5 * N + nb], div);
+        }
+    });
+    div *= 3.0;
+    const double T = a.macro[(size_t)DR_T * N + n];
+    const double rho = (double)R[(size_t)rr.rho * N + n];
+    double rho_a[M], Y[M], fl[3] = {0.0, 0.0, 0.0}, Cp = 0.0;
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+        Y[s] = (double)R[(size_t)(rr.y + s) * N + n];
+        rho_a[s] = rho * Y[s];
+        const double cpy = cp_spec(mc, s, T) * Y[s];
+        Cp += cpy;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fl[d] = fma(cpy, (double)R[(size_t)(rr.du + 3 * s + d) * N + n], fl[d]);
+    }
+    double dT, drho[M];
+    const double hdot = hrr_node<M, false>(mc, T, rho_a, &dT, drho, nullptr, 0);
+    const double g[3] = {scr[n], scr[N + n], scr[2 * N + n]};
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn == 0.0) {
+        Sd[n] = Sa[n] = 0.0;
+        return;
+    }
+    const double num = hdot + div - rho * (fl[0] * g[0] + fl[1] * g[1] + fl[2] * g[2]);
+    const double sd = num / (rho * Cp * gn);
+    double un = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) un -= (double)R[(size_t)(rr.u + d) * N + n] * g[d];
+    Sd[n] = sd;
+    Sa[n] = sd + un / gn;
+}
+
+template <int M>
+int run_flame_speeds(const StepArgs &a, double *scr, double *Sd, double *Sa)
+{
+    int e = 0;
+    if (a.bc_x == 1) e = launch_one<M>(a, LBMK_K_GHOST);
+    if (!e) e = launch_one<M>(a, LBMK_K_PRE);
+    if (e) return e;
+    k_flame1<M><<<grid_for(a.N), LBMK_BLOCK, 0, a.stream>>>(a, scr);
+    k_flame2<M><<<grid_for(a.N, LBMK_HRR_THREADS), LBMK_HRR_THREADS, 0, a.stream>>>(a, scr, Sd, Sa);
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------
+// Means along the isoline T = T_iso in the plane z = 0 (Eq. (rmean)):
+// marching squares, one thread per cell (x, y)..(x+1, y+1) of the periodic
+// x-y lattice: crossings where T - T_iso changes sign (T >= T_iso counts as
+// above) at the linear interpolation point along the cell edge, with the K
+// fields interpolated alike; two crossings make one straight segment, four
+// are split by the mean of the corners; each segment adds its length and
+// its length times the mean of its ends' distance from (cx, cy) and field
+// values.  Per-block sums in a fixed order: partial [blocks][2 + K].
+// ---------------------------------------------------------------------
+#define LBMK_ISO_MAXK 8
+__global__ void __launch_bounds__(LBMK_HRR_THREADS) k_isoline(int nx, int ny, int N, const double *T, double T_iso,
+                                                               double cx, double cy, int K, const double *fields,
+                                                               double *partial)
+{
+    __shared__ double sh[(2 + LBMK_ISO_MAXK) * LBMK_HRR_THREADS];
+    const int t = threadIdx.x, W = 2 + K;
+    double acc[2 + LBMK_ISO_MAXK];
+    for (int k = 0; k < W; ++k) acc[k] = 0.0;
+    const int cell = blockIdx.x * LBMK_HRR_THREADS + t;
+    if (cell < nx * ny) {
+        const int x = cell % nx, y = cell / nx;
+        const int ox[4] = {0, 1, 1, 0}, oy[4] = {0, 0, 1, 1};
+        int idx[4];
+        double v[4];
+        for (int c = 0; c < 4; ++c) {
+            idx[c] = (x + ox[c]) % nx + nx * ((y + oy[c]) % ny);
+            v[c] = T[idx[c]];
+        }
+        double px[4], py[4], pf[4][LBMK_ISO_MAXK];
+        int ne = 0;
+        for (int e = 0; e < 4; ++e) {
+            const int aa = e, bb = (e + 1) % 4;
+            if ((v[aa] >= T_iso) == (v[bb] >= T_iso)) continue;
+            const double f = (T_iso - v[aa]) / (v[bb] - v[aa]);
+            px[ne] = x + ox[aa] + f * (ox[bb] - ox[aa]);
+            py[ne] = y + oy[aa] + f * (oy[bb] - oy[aa]);
+            for (int k = 0; k < K; ++k) {
+                const double fa = fields[(size_t)k * N + idx[aa]], fb = fields[(size_t)k * N + idx[bb]];
+                pf[ne][k] = fa + f * (fb - fa);
+            }
+            ++ne;
+        }
+        int pr[2][2] = {{0, 1}, {2, 3}}, np = ne == 2 ? 1 : (ne == 4 ? 2 : 0);
+        if (ne == 4) {
+            const double vc = 0.25 * (v[0] + v[1] + v[2] + v[3]);
+            if ((vc >= T_iso) != (v[0] >= T_iso)) {       // corners 0 and 2 cut off
+                pr[0][0] = 3; pr[0][1] = 0; pr[1][0] = 1; pr[1][1] = 2;
+            }
+        }
+        for (int q = 0; q < np; ++q) {
+            const int i = pr[q][0], j = pr[q][1];
+            const double L = sqrt((px[i] - px[j]) * (px[i] - px[j]) + (py[i] - py[j]) * (py[i] - py[j]));
+            const double Ri = sqrt((px[i] - cx) * (px[i] - cx) + (py[i] - cy) * (py[i] - cy));
+            const double Rj = sqrt((px[j] - cx) * (px[j] - cx) + (py[j] - cy) * (py[j] - cy));
+            acc[0] += L;
+            acc[1] += L * 0.5 * (Ri + Rj);
+            for (int k = 0; k < K; ++k) acc[2 + k] += L * 0.5 * (pf[i][k] + pf[j][k]);
+        }
+    }
+    for (int k = 0; k < W; ++k) sh[k * LBMK_HRR_THREADS + t] = acc[k];
+    __syncthreads();
+    for (int h = LBMK_HRR_THREADS / 2; h > 0; h >>= 1) {
+        if (t < h)
+            for (int k = 0; k < W; ++k) sh[k * LBMK_HRR_THREADS + t] += sh[k * LBMK_HRR_THREADS + t + h];
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int k = 0; k < W; ++k) partial[(size_t)blockIdx.x * W + k] = sh[k * LBMK_HRR_THREADS];
+}
+
 }  // namespace
 
 #define LBMK_DISPATCH(M_, CALL)                     \

@@ -105,7 +105,8 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
             "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe",
-            "lbm_adjoint_workspace_bytes", "lbm_adjoint_step", "lbm_heat_release_gradient"]
+            "lbm_adjoint_workspace_bytes", "lbm_adjoint_step", "lbm_heat_release_gradient",
+            "lbm_flame_speeds", "lbm_isoline_means"]
 
 
 def library_path() -> str:
@@ -273,6 +274,20 @@ def lbm_heat_release_gradient(ctx, nsteps: int, checkpoint_every: int, J: np.nda
                                           dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
                                           C.c_void_p(dT0_ptr) if dT0_ptr else None, C.c_void_p(ws_ptr),
                                           int(ws_bytes))
+
+
+_lib.lbm_flame_speeds.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.lbm_isoline_means.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                   _dp]
+
+
+def lbm_flame_speeds(ctx, Sd_ptr: int, Sa_ptr: int) -> int:
+    return _lib.lbm_flame_speeds(ctx, C.c_void_p(Sd_ptr), C.c_void_p(Sa_ptr))
+
+
+def lbm_isoline_means(ctx, T_ptr: int, T_iso: float, cx: float, cy: float, K: int, fields_ptr, out: np.ndarray) -> int:
+    return _lib.lbm_isoline_means(ctx, C.c_void_p(T_ptr), float(T_iso), float(cx), float(cy), int(K),
+                                  C.c_void_p(fields_ptr) if fields_ptr else None, out.ctypes.data_as(_dp))
 
 
 _lib.lbm_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, _dp, C.c_void_p]
@@ -571,6 +586,31 @@ class Solver:
                "lbm_heat_release_gradient")
         del ws
         return float(J[0]), dA[:self.R], dT0, nb
+
+    @_on_device
+    def flame_speeds(self, device: bool = False):
+        """(S_d, S_a) [N] of the current state (see lbm_flame_speeds)."""
+        if device:
+            Sd = self.torch.empty(self.N, dtype=self.torch.float64, device=self.device)
+            Sa = self.torch.empty_like(Sd)
+            _check(lbm_flame_speeds(self.ctx, Sd.data_ptr(), Sa.data_ptr()), "lbm_flame_speeds")
+        else:
+            Sd, Sa = np.empty(self.N), np.empty(self.N)
+            _check(lbm_flame_speeds(self.ctx, Sd.ctypes.data, Sa.ctypes.data), "lbm_flame_speeds")
+        return Sd, Sa
+
+    @_on_device
+    def isoline_means(self, T, T_iso: float, cx: float, cy: float, fields=()):
+        """{A, mean R, means of fields} along T = T_iso (see lbm_isoline_means);
+        T and fields: float64 device tensors [N]."""
+        torch = self.torch
+        K = len(fields)
+        Td = T.contiguous().to(device=self.device, dtype=torch.float64)
+        F = torch.stack([f.to(device=self.device, dtype=torch.float64) for f in fields]).contiguous() if K else None
+        out = np.zeros(2 + K)
+        _check(lbm_isoline_means(self.ctx, Td.data_ptr(), T_iso, cx, cy, K, F.data_ptr() if K else None, out),
+               "lbm_isoline_means")
+        return out
 
     @_on_device
     def chemistry_at(self, rho_a, T):

@@ -12,6 +12,7 @@ from .configs import (  # noqa: F401
     config1_problem,
     flame1d_problem,
     adjoint_flame_problem,
+    circular_flame_problem,
     sphere3d_problem,
     small_periodic_problem,
     batched_flames_lengths,

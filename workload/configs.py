@@ -326,6 +326,29 @@ def adjoint_flame_problem(nx: int = 512, ny: int = 4, nz: int = 4, T_slab: float
     return p
 
 
+def circular_flame_problem(n: int = 512, nz: int = 1, R_ig: float = 48.0, A0: float = 0.05, n0: int = 4,
+                           phi: float = 0.6, T_u: float = 298.0, T_b: float = 1844.27, width: float = 1.5,
+                           chem_scale: float = MECH9_CHEM_SCALE) -> Problem:
+    """The circular expanding flame of Sec. 5b on a periodic quasi-2D box
+    n x n x nz: the mixture of equivalence ratio phi at T_u, and inside
+    R(theta) = R_ig (1 + A0 cos(4 n0 theta)) around the box centre
+    (Eq. (cflamePerturbation)) the same composition at T_b, joined by a
+    tanh profile of the given width (nodes); uniform pressure, at rest."""
+    sp, mech = mech9(chem_scale)
+    N = n * n * nz
+    X = _normalise_with_noise(phi_mixture(phi), N, None)
+    idx = np.arange(N)
+    x = (idx % n).astype(float)
+    y = ((idx // n) % n).astype(float)
+    c = (n - 1) / 2.0
+    th = np.arctan2(y - c, x - c)
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2)
+    Rt = R_ig * (1.0 + A0 * np.cos(4 * n0 * th))
+    T = T_u + (T_b - T_u) * 0.5 * (1.0 - np.tanh((r - Rt) / width))
+    return Problem(f"circular_flame_{n}x{n}x{nz}_M9", LatticeSpec(n, n, nz, BC_PERIODIC), sp, mech,
+                   InitFields(X=X, T=T, u=None, P=mech.P0), steps=1000)
+
+
 def sphere3d_problem(n: int = 256, radius: float = 20.0, T_u: float = MECH9_T_UNBURNT,
                      T_hot: float = 2000.0, seed: int = 1703,
                      chem_scale: float = MECH9_CHEM_SCALE, shape=None) -> Problem:
