@@ -594,6 +594,11 @@ def run_ours(args):
     if not args.skip_cflame:
         cflame = circular_flame_run(lbm, torch, stream, precision)
 
+    flames48 = None
+    if not args.skip_flames:
+        flames48 = flames_measure(lbm, w, replicas, precision, args.flames_steps, args.warmup, stream, dist, rank,
+                                  world, autotune=not args.skip_autotune)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = _cpu_oracle_sample()
@@ -627,6 +632,7 @@ def run_ours(args):
             "heat_release": hrr,
             "adjoint": adjoint,
             "circular_flame": cflame,
+            "flames48": flames48,
             "mixed_over_fp64": (mlups / fp64["mlups"]) if fp64 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -638,13 +644,91 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def flames_measure(lbm, w, replicas, precision, K, warmup, stream, dist=None, rank=0, world=1,
+                   autotune=True, clk=None):
+    """The batched quasi-1D flames (48 ragged flames side by side in one
+    lattice) stepped K times three ways -- one set of launches per step,
+    those launches replayed from a captured CUDA graph, and one persistent
+    cooperative launch for all K steps -- against the same flames stepped
+    one flame at a time (one context per flame, sharing the batch's
+    tables).  With N ranks the flames are split across them by node count
+    (no collective on the data path); MLUPS count all ranks' nodes over the
+    slowest rank."""
+    import torch
+    L_all, phi_all = w.batched_flames_lengths()
+    shards = replicas.shard_lengths(L_all, world)
+    mine = shards[rank]
+    prob = w.batched_flames_problem(lengths=[L_all[k] for k in mine], phis=[phi_all[k] for k in mine])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        return replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+
+    batch = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
+    # launch shapes and the persistent tile length, outside the timed region
+    blocks = batch.autotune(trials=3) if autotune else None
+    tile = batch.autotune_persistent(steps=4) if autotune else 1
+    batch.step(warmup)
+    batch.step_persistent(warmup, tile_mult=tile)
+    ms_plain = timed(lambda: batch.step_async(K))
+    batch.step_graph(2)                           # capture outside the timed region
+    assert batch.sync() == lbm.LBM_OK
+    ms_graph = timed(lambda: batch.step_graph(K))
+    assert batch.sync() == lbm.LBM_OK
+    ms_pers = timed(lambda: batch.step_persistent(K, tile_mult=tile))
+    T = batch.moments(lbm.LBM_F_T)["T"]
+    finite = bool(np.isfinite(T).all())
+    refs = batch.references() if precision != lbm.LBM_FP64 else None
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+
+    flames = []
+    for k in range(len(prob.lattice.seg_nx)):
+        fk = w.flame_of_batch(prob, k)
+        s = lbm.Solver.from_problem(fk, precision=precision, stream=stream, init=False)
+        if refs is not None:
+            s.set_references(refs)
+        s.init(fk.init.X, fk.init.T, fk.init.u, fk.init.P)
+        s.step(warmup)
+        flames.append(s)
+
+    def loop():
+        for _ in range(K):
+            for s in flames:
+                s.step_async(1)
+    ms_loop = timed(loop)
+    for s in flames:
+        assert s.sync() == lbm.LBM_OK
+        s.close()
+
+    nodes = [sum(int(L_all[k]) for k in shards[r]) * prob.lattice.ny * prob.lattice.nz for r in range(world)]
+    mlups = lambda ms: replicas.whole_job_mlups(nodes, K, ms)
+    best = min(("graph", ms_graph), ("persistent", ms_pers), key=lambda t: t[1])
+    return {"workload": f"flames{len(L_all)}_M9", "nodes": sum(nodes), "flames": len(L_all),
+            "lengths": [int(min(L_all)), int(max(L_all))], "cross_section": "4x4", "steps": K,
+            "persistent_mlups": mlups(ms_pers), "batched_graph_mlups": mlups(ms_graph),
+            "batched_plain_mlups": mlups(ms_plain), "loop_single_flames_mlups": mlups(ms_loop),
+            "best": best[0], "best_mlups": mlups(best[1]), "speedup_vs_loop": ms_loop / best[1],
+            "persistent_over_graph": ms_graph / ms_pers, "persistent_chunk_nodes": 32 * tile,
+            "autotuned_blocks": blocks, "temperature_finite": finite,
+            "ms": {"plain": ms_plain, "graph": ms_graph, "persistent": ms_pers, "loop": ms_loop},
+            "launches": {"plain": K * launches_per_step(True), "graph": K * launches_per_step(True),
+                         "persistent": 1, "loop": K * len(prob.lattice.seg_nx) * launches_per_step(True)}}
+
+
 def run_flames(args):
-    """The batched quasi-1D flames: 48 ragged flames side by side in one
-    lattice, stepped with one set of launches per step (plain and through a
-    captured CUDA graph), against the same flames stepped one flame at a
-    time (one context per flame, sharing the batch's tables).  With N ranks
-    the flames are split across them by node count (no collective on the
-    data path); the value counts all ranks' nodes over the slowest rank."""
+    """The batched flames as a line of their own (see flames_measure); the
+    value is the faster of the graph and the persistent launch."""
     import torch
     import workload as w
     from paper_2101_01702_gb300 import build
@@ -662,76 +746,22 @@ def run_flames(args):
 
     modes = {"mixed": lbm.LBM_MIXED, "mixed_fast": lbm.LBM_MIXED_FAST, "fp64": lbm.LBM_FP64}
     precision = modes[args.precision]
-    L_all, phi_all = w.batched_flames_lengths()
-    shards = replicas.shard_lengths(L_all, world)
-    mine = shards[rank]
-    prob = w.batched_flames_problem(lengths=[L_all[k] for k in mine], phis=[phi_all[k] for k in mine])
-    N = prob.lattice.n_nodes
-    K = args.steps
     stream = torch.cuda.Stream()
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        return replicas.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-
-    batch = lbm.Solver.from_problem(prob, precision=precision, stream=stream)
-    blocks = None if args.skip_autotune else batch.autotune(trials=3)   # launch shapes, outside the timed region
-    batch.step(args.warmup)
     with ClockSampler(local) as clk:
-        ms_plain = timed(lambda: batch.step_async(K))
-        batch.step_graph(2)                       # capture outside the timed region
-        assert batch.sync() == lbm.LBM_OK
-        ms_graph = timed(lambda: batch.step_graph(K))
-    assert batch.sync() == lbm.LBM_OK
-    refs = batch.references() if precision != lbm.LBM_FP64 else None
-    batch.close()
-    del batch
-    torch.cuda.empty_cache()
-
-    flames = []
-    for k in range(len(prob.lattice.seg_nx)):
-        fk = w.flame_of_batch(prob, k)
-        s = lbm.Solver.from_problem(fk, precision=precision, stream=stream, init=False)
-        if refs is not None:
-            s.set_references(refs)
-        s.init(fk.init.X, fk.init.T, fk.init.u, fk.init.P)
-        s.step(args.warmup)
-        flames.append(s)
-
-    def loop():
-        for _ in range(K):
-            for s in flames:
-                s.step_async(1)
-    ms_loop = timed(loop)
-    for s in flames:
-        assert s.sync() == lbm.LBM_OK
-        s.close()
-
-    nodes = [sum(int(L_all[k]) for k in shards[r]) * prob.lattice.ny * prob.lattice.nz for r in range(world)]
-    mlups = lambda ms: replicas.whole_job_mlups(nodes, K, ms)
+        r = flames_measure(lbm, w, replicas, precision, args.steps, args.warmup, stream, dist, rank, world,
+                           autotune=not args.skip_autotune)
+    K = args.steps
     if rank == 0:
-        line = {"metric": "MLUPS (batched quasi-1D flames, one launch set per step)", "value": mlups(ms_graph),
+        line = {"metric": "MLUPS (batched quasi-1D flames)", "value": r["best_mlups"],
                 "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": args.warmup,
-                "ms_per_step": ms_graph / K, "higher_is_better": True,
+                "ms_per_step": r["ms"][r["best"]] / K, "higher_is_better": True,
                 "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
                 "dtype": "f32+f64" if precision != lbm.LBM_FP64 else "f64", "data": "synthetic",
-                "config": {"workload": f"flames{len(L_all)}_M9_{args.precision}", "nodes": sum(nodes),
-                           "flames": len(L_all), "lengths": [int(min(L_all)), int(max(L_all))],
-                           "cross_section": "4x4", "parallelism": f"flames split over {world} ranks"
-                           if world > 1 else "single_gpu"},
-                "batched_graph_mlups": mlups(ms_graph), "batched_plain_mlups": mlups(ms_plain),
-                "loop_single_flames_mlups": mlups(ms_loop), "speedup_vs_loop": ms_loop / ms_graph,
-                "autotuned_blocks": blocks,
-                "gpu_launches": K * launches_per_step(True),
+                "config": {"workload": f"{r['workload']}_{args.precision}", "nodes": r["nodes"],
+                           "flames": r["flames"], "lengths": r["lengths"], "cross_section": "4x4",
+                           "parallelism": f"flames split over {world} ranks" if world > 1 else "single_gpu"},
+                "flames48": r,
+                "gpu_launches": r["launches"][r["best"]],
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -795,6 +825,8 @@ def main():
     ap.add_argument("--skip-hrr", action="store_true", help="skip the heat-release sensitivity measurement")
     ap.add_argument("--skip-adjoint", action="store_true", help="skip the gradients through time (512x4x4, 2000 steps)")
     ap.add_argument("--skip-cflame", action="store_true", help="skip the perturbed circular flame (512x512x1)")
+    ap.add_argument("--skip-flames", action="store_true", help="skip the batched-flames key of the default line")
+    ap.add_argument("--flames-steps", type=int, default=20, help="steps of the batched-flames key")
     ap.add_argument("--workload", default="sphere3d", choices=["sphere3d", "flames48"])
     ap.add_argument("--cpu-legs", action="store_true",
                     help="instead of timing the GPU: the oracle's timed legs (64x4x4 200 steps, 32^3 1000 steps, "

@@ -48,7 +48,8 @@ enum {
     LBM_ERR_NEGATIVE = -5,     /* a species density fell below -1e-10 rho           */
     LBM_ERR_PIVOT = -6,        /* non-finite pivot in the Stefan-Maxwell elimination */
     LBM_ERR_BOUNDS = -7,       /* checked builds: an index left its buffer (a bug)  */
-    LBM_ERR_UNSUPPORTED = -8   /* valid request this build does not provide        */
+    LBM_ERR_UNSUPPORTED = -8,  /* valid request this build does not provide        */
+    LBM_ERR_BARRIER = -9       /* lbm_step_persistent: a grid barrier gave up waiting */
 };
 
 enum { LBM_BC_PERIODIC = 0, LBM_BC_EQ_ZEROGRAD_U0LEFT = 1 };
@@ -220,6 +221,31 @@ int lbm_step_async(lbm_ctx *ctx, int n);
  * those of lbm_step_async.  The stream must not be the legacy default
  * stream (LBM_ERR_UNSUPPORTED).  Errors surface at lbm_sync(). */
 int lbm_step_graph(lbm_ctx *ctx, int n);
+
+/* n time steps in ONE persistent, cooperative kernel launch (the paper has
+ * no counterpart: a launch structure for batches of small lattices, such as
+ * the quasi-1D flames of Sec. 5a side by side).  The blocks stay resident;
+ * in each phase of a step (ghost planes, the per-node record, G, the
+ * energy collision, the species collision) their warps take chunks of
+ * tile_mult x 32 consecutive nodes from a queue, and all meet at a grid
+ * barrier before the next phase.  Results are bit for bit those of
+ * lbm_step in the mixed units; in the double unit they agree to rounding
+ * (the compiler may fuse a multiply and an add in this kernel where it does
+ * not in the separate ones: about one unit in the last place per step).  Each barrier polls a device word at most spin_cap times
+ * (0: 1 << 24, about two seconds); a block that runs out records
+ * LBM_ERR_BARRIER and returns, the others then run out at the next barrier,
+ * so the launch always ends -- the state is then partly stepped and must be
+ * re-initialised or restored.  tile_mult >= 1.  Waits for the stream and
+ * returns like lbm_sync (LBM_ERR_BARRIER after a timeout); LBM_ERR_ARG for
+ * n < 0 or tile_mult < 1. */
+int lbm_step_persistent(lbm_ctx *ctx, int n, int tile_mult, unsigned spin_cap);
+
+/* Picks the tile length of lbm_step_persistent (tile_mult in 1, 2, 4, 8)
+ * by timing `steps` persistent steps of each on a copy of the current state
+ * (kept aside and put back, with the temperature row: the state is
+ * unchanged); *tile_mult_out receives the fastest.  Allocates a copy of the
+ * state for the duration of the call.  Waits for the stream. */
+int lbm_autotune_persistent(lbm_ctx *ctx, int steps, int *tile_mult_out);
 
 /* Autotuner of the launch shapes (the paper has no counterpart): times
  * each kernel of the step on the context's current state with every

@@ -16,7 +16,8 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "liblbm.so"
 LIB_CHECKED = BUILD / "liblbm_checked.so"   # every geometry-derived index checked (tests)
-SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_mixed_fast.cu", "k_fixed_scratch.cu", "k_probe.cu", "k_adjoint.cu"]
+SOURCES = ["lbm_api.cu", "k_fp64.cu", "k_mixed.cu", "k_mixed_fast.cu", "k_fixed_scratch.cu", "k_probe.cu", "k_adjoint.cu",
+           "k_persist_fp64.cu", "k_persist_mixed.cu", "k_persist_mixed_fast.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

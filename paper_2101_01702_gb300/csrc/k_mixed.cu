@@ -6,8 +6,10 @@ namespace lbmk {
 
 int upload_mixed(int slot, const MechConst &mc, cudaStream_t s)
 {
-    return (int)cudaMemcpyToSymbolAsync(c_mech, &mc, sizeof(MechConst), (size_t)slot * sizeof(MechConst),
-                                        cudaMemcpyHostToDevice, s);
+    // this unit's tables and those of its persistent kernel's unit
+    const int e = (int)cudaMemcpyToSymbolAsync(c_mech, &mc, sizeof(MechConst), (size_t)slot * sizeof(MechConst),
+                                               cudaMemcpyHostToDevice, s);
+    return e ? e : upload_persistent_mixed(slot, mc, s);
 }
 
 int init_mixed(const StepArgs &a, const double *X, const double *T, const double *u, double P)

@@ -65,15 +65,16 @@ const lbmk::PrecisionOps kOps[3] = {
     {lbmk::upload_fp64, lbmk::init_fp64, lbmk::step_fp64, lbmk::moments_fp64, lbmk::ref_stats_fp64,
      lbmk::launch_one_fp64, lbmk::hrr_fp64,
      lbmk::chem_at_fp64, lbmk::temperature_at_fp64,
-     lbmk::hrr_adj_fp64, lbmk::hrr_adj_gather_fp64, lbmk::flame_fp64},
+     lbmk::hrr_adj_fp64, lbmk::hrr_adj_gather_fp64, lbmk::flame_fp64, lbmk::persistent_fp64},
     {lbmk::upload_mixed, lbmk::init_mixed, lbmk::step_mixed, lbmk::moments_mixed, lbmk::ref_stats_mixed,
      lbmk::launch_one_mixed, lbmk::hrr_mixed,
      lbmk::chem_at_mixed, lbmk::temperature_at_mixed,
-     lbmk::hrr_adj_mixed, lbmk::hrr_adj_gather_mixed, lbmk::flame_mixed},
+     lbmk::hrr_adj_mixed, lbmk::hrr_adj_gather_mixed, lbmk::flame_mixed, lbmk::persistent_mixed},
     {lbmk::upload_mixed_fast, lbmk::init_mixed_fast, lbmk::step_mixed_fast, lbmk::moments_mixed_fast,
      lbmk::ref_stats_mixed_fast, lbmk::launch_one_mixed_fast, lbmk::hrr_mixed_fast,
      lbmk::chem_at_mixed_fast, lbmk::temperature_at_mixed_fast,
-     lbmk::hrr_adj_mixed_fast, lbmk::hrr_adj_gather_mixed_fast, lbmk::flame_mixed_fast},
+     lbmk::hrr_adj_mixed_fast, lbmk::hrr_adj_gather_mixed_fast, lbmk::flame_mixed_fast,
+     lbmk::persistent_mixed_fast},
 };
 const lbmk::PrecisionOps &ops(int precision) { return kOps[precision]; }
 
@@ -147,6 +148,7 @@ int map_status(unsigned bits)
     if (bits & LBMK_BIT_NEGATIVE) return LBM_ERR_NEGATIVE;
     if (bits & LBMK_BIT_PIVOT) return LBM_ERR_PIVOT;
     if (bits & LBMK_BIT_BOUNDS) return LBM_ERR_BOUNDS;
+    if (bits & LBMK_BIT_BARRIER) return LBM_ERR_BARRIER;
     return LBM_OK;
 }
 
@@ -378,8 +380,9 @@ int lbm_create(const lbm_lattice *lat, const lbm_species *sp, const lbm_mechanis
     c->mc = mc;
     c->lat.seg_nx = nullptr;     // read here only
     for (int k = 0; k < LBMK_NKERNELS; ++k) c->bs[k] = LBMK_BLOCK;
-    int st = check_cuda(cudaMalloc((void **)&c->status, 16));
-    if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16, c->stream));
+    // the status word, then (at byte 16) the persistent step's barrier state
+    int st = check_cuda(cudaMalloc((void **)&c->status, 16 + sizeof(GridBarrier)));
+    if (st == LBM_OK) st = check_cuda(cudaMemsetAsync(c->status, 0, 16 + sizeof(GridBarrier), c->stream));
     if (st == LBM_OK && lat->nseg > 1) {
         // per-x and per-lattice ranges of the batch
         const int nx = lat->nx, ns = lat->nseg;
@@ -515,6 +518,69 @@ int lbm_step_graph(lbm_ctx *c, int n)
     for (; left >= 2; left -= 2)          // two steps leave cur where it was
         if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return LBM_ERR_CUDA;
     return left == 1 ? lbm_step_async(c, 1) : LBM_OK;
+}
+
+int lbm_step_persistent(lbm_ctx *c, int n, int tile_mult, unsigned spin_cap)
+{
+    if (!c || n < 0 || tile_mult < 1) return LBM_ERR_ARG;
+    const int od = on_ctx_device(c);
+    if (od != LBM_OK) return od;
+    if (n == 0) return lbm_sync(c);
+    // the barrier state follows the status word's 16 bytes
+    GridBarrier *bar = reinterpret_cast<GridBarrier *>(c->status + 4);
+    int st = check_cuda(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), c->stream));
+    if (st != LBM_OK) return st;
+    const int e = ops(c->lat.precision).persistent(args_of(c), n, tile_mult, bar, spin_cap ? spin_cap : (1u << 24));
+    if (e == (int)cudaErrorNotSupported) return LBM_ERR_UNSUPPORTED;
+    if (e) return LBM_ERR_CUDA;
+    if (n & 1) c->cur = 1 - c->cur;
+    return lbm_sync(c);
+}
+
+int lbm_autotune_persistent(lbm_ctx *c, int steps, int *tile_mult_out)
+{
+    if (!c || steps < 1 || !tile_mult_out) return LBM_ERR_ARG;
+    int st = lbm_sync(c);
+    if (st != LBM_OK) return st;
+    const size_t Tb = (size_t)c->N * sizeof(double);
+    const int cur0 = c->cur;
+    void *keep = nullptr;
+    if (cudaMalloc(&keep, c->pop_bytes + Tb) != cudaSuccess) return LBM_ERR_CUDA;
+    double *Trow = c->macro + (size_t)DR_T * c->N;
+    st = copy_d2d(keep, c->buf[cur0], c->pop_bytes, c->stream);
+    if (st == LBM_OK) st = copy_d2d((char *)keep + c->pop_bytes, Trow, Tb, c->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = LBM_ERR_CUDA;
+    static const int cand[4] = {1, 2, 4, 8};
+    float best = 0.f;
+    int best_t = 1;
+    for (int j = 0; j < 4 && st == LBM_OK; ++j) {
+        for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {    // once to warm up, once timed
+            c->cur = cur0;
+            st = copy_d2d(c->buf[cur0], keep, c->pop_bytes, c->stream);
+            if (st == LBM_OK) st = copy_d2d(Trow, (char *)keep + c->pop_bytes, Tb, c->stream);
+            if (st == LBM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
+            if (st == LBM_OK) st = lbm_step_persistent(c, steps, cand[j], 0);
+            if (st == LBM_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = LBM_ERR_CUDA;
+        }
+        float ms = 0.f;
+        if (st == LBM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = LBM_ERR_CUDA;
+        if (st == LBM_OK && (best == 0.f || ms < best)) {
+            best = ms;
+            best_t = cand[j];
+        }
+    }
+    c->cur = cur0;
+    const int st2 = copy_d2d(c->buf[cur0], keep, c->pop_bytes, c->stream);
+    const int st3 = copy_d2d(Trow, (char *)keep + c->pop_bytes, Tb, c->stream);
+    const int st4 = check_cuda(cudaStreamSynchronize(c->stream));
+    cudaFree(keep);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == LBM_OK) st = st2 != LBM_OK ? st2 : (st3 != LBM_OK ? st3 : st4);
+    if (st == LBM_OK) *tile_mult_out = best_t;
+    return st;
 }
 
 int lbm_autotune(lbm_ctx *c, int trials, int *block_out)
@@ -1121,6 +1187,7 @@ const char *lbm_strerror(int s)
     case LBM_ERR_PIVOT: return "non-finite pivot in the Stefan-Maxwell solve";
     case LBM_ERR_BOUNDS: return "index out of bounds (checked build)";
     case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case LBM_ERR_BARRIER: return "a grid barrier of the persistent step gave up waiting";
     default: return "unknown status";
     }
 }

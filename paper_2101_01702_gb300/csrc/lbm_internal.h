@@ -18,6 +18,14 @@
 #define LBMK_BIT_NEGATIVE 4u
 #define LBMK_BIT_PIVOT 8u
 #define LBMK_BIT_BOUNDS 16u     // checked builds: an index derived from the geometry left its buffer
+#define LBMK_BIT_BARRIER 32u    // the persistent step: a grid barrier gave up waiting (its poll limit ran out)
+
+// Grid-wide barrier state of the persistent step (device, zeroed before a
+// launch): blocks that have arrived, the generation they wait to change,
+// and the next chunk of nodes the current phase hands out.
+struct GridBarrier {
+    unsigned count, gen, next;
+};
 
 // Per-node record in the macro buffer: macro_double_rows(M) rows of
 // doubles, then rec_rows(M).total rows of the storage type (float in mixed
@@ -241,6 +249,17 @@ inline int isoline_blocks(long long cells) { return (int)((cells + LBMK_HRR_THRE
 int isoline_fp64(int nx, int ny, int N, const double *T, double T_iso, double cx, double cy, int K,
                  const double *fields, double *partial, double *out, cudaStream_t s);
 
+// nsteps full time steps in one cooperative launch (lbm_step_persistent):
+// every node in tiles of tile_mult blocks' worth of nodes, the phases
+// separated by grid barriers that poll at most cap times; bar: device
+int persistent_fp64(const StepArgs &a, int nsteps, int tile_mult, GridBarrier *bar, unsigned cap);
+int persistent_mixed(const StepArgs &a, int nsteps, int tile_mult, GridBarrier *bar, unsigned cap);
+int persistent_mixed_fast(const StepArgs &a, int nsteps, int tile_mult, GridBarrier *bar, unsigned cap);
+// the persistent units' constant tables (called by upload_fp64 and the like)
+int upload_persistent_fp64(int slot, const MechConst &mc, cudaStream_t s);
+int upload_persistent_mixed(int slot, const MechConst &mc, cudaStream_t s);
+int upload_persistent_mixed_fast(int slot, const MechConst &mc, cudaStream_t s);
+
 // one kernel of the step (LBMK_K_*) with the block size a.bs[kernel]
 int launch_one_fp64(const StepArgs &a, int kernel);
 int launch_one_mixed(const StepArgs &a, int kernel);
@@ -261,6 +280,7 @@ struct PrecisionOps {
     int (*hrr_adj)(const StepArgs &a, double *adj);
     int (*hrr_adj_gather)(const StepArgs &a, const double *adj, int s, double *out);
     int (*flame)(const StepArgs &a, double *scratch, double *Sd, double *Sa);
+    int (*persistent)(const StepArgs &a, int nsteps, int tile_mult, GridBarrier *bar, unsigned cap);
 };
 }  // namespace lbmk
 

@@ -189,6 +189,20 @@ __device__ __forceinline__ bool index_ok(bool ok, unsigned *status)
 #endif
 }
 
+// Populations and ghost planes are read through the read-only data path
+// (__ldg) in the per-phase kernels, none of which reads what it writes.
+// The persistent kernel writes, within its one launch, what its later
+// phases read, so its units build with LBMK_COHERENT_LOADS=1: plain loads,
+// ordered by the grid barrier's fences.
+#ifndef LBMK_COHERENT_LOADS
+#define LBMK_COHERENT_LOADS 0
+#endif
+#if LBMK_COHERENT_LOADS
+#define LBMK_LDG(p_) (*(p_))
+#else
+#define LBMK_LDG(p_) __ldg(p_)
+#endif
+
 // ---------------------------------------------------------------------
 // Population storage (see pop_bytes_for).
 // ---------------------------------------------------------------------
@@ -213,9 +227,9 @@ __device__ __forceinline__ Real load_sf(const MechConst &mc, const PopView &v, i
 {
 #if LBMK_MIXED
     if (i == REST) return (Real)v.rest()[(size_t)s * v.N + idx];
-    return __ldg(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx) + mc.ref[s][i];
+    return LBMK_LDG(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx) + mc.ref[s][i];
 #else
-    return __ldg(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
+    return LBMK_LDG(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
 #endif
 }
 
@@ -225,9 +239,9 @@ __device__ __forceinline__ Real load_sf(const MechConst &mc, const PopView &v, i
 __device__ __forceinline__ Real load_raw_sf(const PopView &v, int s, int i, size_t idx)
 {
 #if LBMK_MIXED
-    return __ldg(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx);
+    return LBMK_LDG(v.mov() + ((size_t)s * LBMK_Q + i) * v.N + idx);
 #else
-    return __ldg(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
+    return LBMK_LDG(static_cast<const double *>(v.buf) + ((size_t)s * LBMK_Q + i) * v.N + idx);
 #endif
 }
 #if LBMK_MIXED
@@ -249,9 +263,9 @@ __device__ __forceinline__ double load_sf_d(const MechConst &mc, const PopView &
 __device__ __forceinline__ double load_g(const PopView &v, int i, size_t idx)
 {
 #if LBMK_MIXED
-    return __ldg(v.g() + (size_t)i * v.N + idx);
+    return LBMK_LDG(v.g() + (size_t)i * v.N + idx);
 #else
-    return __ldg(static_cast<const double *>(v.buf) + ((size_t)v.M * LBMK_Q + i) * v.N + idx);
+    return LBMK_LDG(static_cast<const double *>(v.buf) + ((size_t)v.M * LBMK_Q + i) * v.N + idx);
 #endif
 }
 
@@ -302,7 +316,7 @@ __device__ __forceinline__ Src src_of(int i, const PullIdx &p, const StepArgs &a
 __device__ __forceinline__ double load_ghost(const StepArgs &a, int plane_idx, int s, int i, size_t yz)
 {
     const size_t plane = (size_t)a.ny * a.nz;
-    return __ldg(static_cast<const double *>(a.ghost) + ((size_t)(plane_idx * (a.M + 1) + s) * LBMK_Q + i) * plane +
+    return LBMK_LDG(static_cast<const double *>(a.ghost) + ((size_t)(plane_idx * (a.M + 1) + s) * LBMK_Q + i) * plane +
                  yz);
 }
 
@@ -753,12 +767,11 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_INIT_MINB) k_init(StepArgs a,
 // post-collision moments of the adjacent boundary node, u = 0 on the left.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
+__device__ __forceinline__ void ghost_node(const StepArgs &a, int t)
 {
     const MechConst &mc = c_mech[a.slot];
     const int plane = a.ny * a.nz;
     const int nlat = a.nseg > 1 ? a.nseg : 1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * nlat * plane) return;
     const int gp = t / plane, yz = t % plane;          // ghost plane 2k + side of lattice k
     const int side = gp & 1, k = gp >> 1;
@@ -799,6 +812,12 @@ __global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
     if (side == 0) u[0] = u[1] = u[2] = 0.0;
     double *gh = static_cast<double *>(a.ghost) + (size_t)gp * (M + 1) * LBMK_Q * plane;
     equilibria<M>(mc, rho_a, u, T, [&](int s, int i, double val) { gh[((size_t)s * LBMK_Q + i) * plane + yz] = val; });
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK) k_ghost(StepArgs a)
+{
+    ghost_node<M>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------
@@ -1053,11 +1072,9 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_MOM_MINB) k_moments(StepArgs 
 // writes the per-node record (all rows but the production rates).
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
+__device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
 {
     const MechConst &mc = c_mech[a.slot];
-    Node nd;
-    if (!node_of(nd, a)) return;
     PullIdx p;
     make_pull(p, nd, a);
     double rho_a[M];
@@ -1297,6 +1314,14 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
     R[(size_t)rr.p * N + n] = (Real)P;
 }
 
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_pre(StepArgs a)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    pre_node<M>(a, nd);
+}
+
 // ---------------------------------------------------------------------
 // Pass 1b: production rates of the record's state (molar_production).
 // ---------------------------------------------------------------------
@@ -1334,10 +1359,8 @@ __global__ void __launch_bounds__(LBMK_MAXBLOCK) k_chem(StepArgs a)
 // gradient d_alpha phi = (1/theta) sum_i w_i c_ia phi(x + c_i).
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_MAXBLOCK) k_grad(StepArgs a)
+__device__ __forceinline__ void grad_node(const StepArgs &a, const Node &nd)
 {
-    Node nd;
-    if (!node_of(nd, a)) return;
     const size_t N = a.N;
     const RecRows rr = rec_rows(M);
     Real *R = rec(a);
@@ -1356,6 +1379,14 @@ __global__ void __launch_bounds__(LBMK_MAXBLOCK) k_grad(StepArgs a)
     Real *G = R + (size_t)rr.g * N;
 #pragma unroll
     for (int k = 0; k < 3; ++k) G[k * N + nd.n] = nup * (Real)3 * d[k];
+}
+
+template <int M>
+__global__ void __launch_bounds__(LBMK_MAXBLOCK) k_grad(StepArgs a)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    grad_node<M>(a, nd);
 }
 
 // ---------------------------------------------------------------------
@@ -1466,7 +1497,7 @@ __global__ void __launch_bounds__(LBMK_MAXBLOCK) k_step_g(StepArgs a)
 // direction, in the storage precision.
 // ---------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
+__device__ __forceinline__ void step_node(const StepArgs &a, const Node &nd)
 {
 #if !LBMK_MIXED
     // y-z factors of the species equilibria for the current row, this
@@ -1479,8 +1510,6 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
     __shared__ WReal sh_w[M * LBMK_BLOCK];
 #endif
     const MechConst &mc = c_mech[a.slot];
-    Node nd;
-    if (!node_of(nd, a)) return;
     const int n = nd.n;
     const size_t N = a.N;
     const RecRows rr = rec_rows(M);
@@ -1690,6 +1719,14 @@ __global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
 #endif
 }
 
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_STEP_MINB) k_step(StepArgs a)
+{
+    Node nd;
+    if (!node_of(nd, a)) return;
+    step_node<M>(a, nd);
+}
+
 // ---------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------
@@ -1738,6 +1775,135 @@ int launch_one(const StepArgs &a, int k)
     }
     return (int)cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------
+// Persistent step: nsteps time steps of every node in one cooperative
+// launch.  Within a phase each warp takes chunks of `chunk` consecutive
+// nodes from a queue (one atomic per chunk), so that SMs whose nodes cost
+// less (fewer Newton iterations, no flame) take more of them; the phases
+// that read a neighbour's value of the same time level -- ghost planes,
+// the record (k_pre), G (k_grad), then both collisions -- are separated by
+// grid barriers, whose last arrival also resets the queue, and the two
+// population buffers swap every step.  A barrier polls at most `cap`
+// times: a block that runs out sets LBMK_BIT_BARRIER and returns, and the
+// others then run out at the next barrier, so the launch always ends.
+// Built only in the units with coherent loads (LBMK_COHERENT_LOADS).
+// ---------------------------------------------------------------------
+#if LBMK_COHERENT_LOADS
+__device__ __forceinline__ bool grid_barrier(GridBarrier *g, unsigned nblocks, unsigned cap, unsigned *status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &g->gen;
+        const unsigned gen = *vgen;                    // read before arriving: only this barrier's last arrival changes it
+        __threadfence();
+        if (atomicAdd(&g->count, 1u) == nblocks - 1) {
+            atomicExch(&g->count, 0u);
+            atomicExch(&g->next, 0u);                  // every block is past its last take
+            __threadfence();
+            atomicAdd(&g->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*vgen == gen) {
+                if (++it > cap) {
+                    flag(status, LBMK_BIT_BARRIER);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Each warp takes chunks of `chunk` consecutive nodes (a multiple of 32)
+// until the queue passes the last node.
+template <int M, class Body>
+__device__ __forceinline__ void tile_loop(const StepArgs &a, int chunk, unsigned *next, Body &&body)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned c = 0;
+        if (lane == 0) c = atomicAdd(next, 1u);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        const long long base = (long long)c * chunk;
+        if (base >= a.N) break;
+        for (int k = lane; k < chunk; k += 32) {
+            Node nd;
+            nd.n = (int)(base + k);
+            if (nd.n >= a.N) break;
+            node_at(nd, a);
+            body(nd);
+        }
+    }
+}
+
+// One time step of the persistent kernel over the buffers of b.
+template <int M>
+__device__ __forceinline__ bool persist_step(const StepArgs &b, int tile, GridBarrier *bar, unsigned nb, unsigned cap)
+{
+    if (b.bc_x == 1) {
+        const int ng = 2 * (b.nseg > 1 ? b.nseg : 1) * b.ny * b.nz;
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) ghost_node<M>(b, g);
+        if (!grid_barrier(bar, nb, cap, b.status)) return false;
+    }
+    tile_loop<M>(b, tile, &bar->next, [&](const Node &nd) { pre_node<M>(b, nd); });
+    if (!grid_barrier(bar, nb, cap, b.status)) return false;
+    tile_loop<M>(b, tile, &bar->next, [&](const Node &nd) { grad_node<M>(b, nd); });
+    if (!grid_barrier(bar, nb, cap, b.status)) return false;
+    // the two collisions read the same inputs and write disjoint sets; the
+    // barrier between them only resets the queue, and separate loops keep
+    // each one's arithmetic as in its own kernel (no values shared)
+    tile_loop<M>(b, tile, &bar->next, [&](const Node &nd) { collide_energy<M>(b, nd); });
+    if (!grid_barrier(bar, nb, cap, b.status)) return false;
+    tile_loop<M>(b, tile, &bar->next, [&](const Node &nd) { step_node<M>(b, nd); });
+    return grid_barrier(bar, nb, cap, b.status);
+}
+
+// a0 steps src -> dst, a1 the same with the buffers swapped: the steps
+// alternate between the two parameter blocks, which the phases then read
+// in place (no per-step copy of the arguments)
+template <int M>
+__global__ void __launch_bounds__(LBMK_BLOCK, LBMK_PRE_MINB) k_persist(StepArgs a0, StepArgs a1, int nsteps, int tile,
+                                                                      GridBarrier *bar, unsigned cap)
+{
+    const unsigned nb = gridDim.x;
+    for (int t = 0; t < nsteps; t += 2) {
+        if (!persist_step<M>(a0, tile, bar, nb, cap)) return;
+        if (t + 1 < nsteps && !persist_step<M>(a1, tile, bar, nb, cap)) return;
+    }
+}
+
+template <int M>
+int run_persistent(const StepArgs &a, int nsteps, int tile_mult, GridBarrier *bar, unsigned cap)
+{
+    if (nsteps < 1 || tile_mult < 1) return (int)cudaErrorInvalidValue;
+    if (!LBMK_FUSE_CHEM) return (int)cudaErrorNotSupported;     // the rates must form inside the collision
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<M>, LBMK_BLOCK, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    const int tile = tile_mult * 32;                   // nodes per warp take
+    const long long tiles = ((long long)a.N + LBMK_BLOCK - 1) / LBMK_BLOCK;
+    const int blocks = (int)std::min<long long>((long long)per_sm * nsm, tiles);
+    if (blocks < 1) return (int)cudaErrorInvalidConfiguration;
+    StepArgs a0 = a, a1 = a;
+    a1.src = a.dst;
+    a1.dst = const_cast<void *>(a.src);
+    int ns = nsteps, tl = tile;
+    GridBarrier *bb = bar;
+    unsigned cc = cap;
+    void *args[] = {(void *)&a0, (void *)&a1, (void *)&ns, (void *)&tl, (void *)&bb, (void *)&cc};
+    return (int)cudaLaunchCooperativeKernel((const void *)k_persist<M>, dim3(blocks), dim3(LBMK_BLOCK), args, 0,
+                                            a.stream);
+}
+#endif  // LBMK_COHERENT_LOADS
 
 template <int M>
 int run_step(const StepArgs &a, cudaEvent_t *ev)

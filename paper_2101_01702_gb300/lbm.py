@@ -30,6 +30,7 @@ LBM_ERR_NEGATIVE = -5
 LBM_ERR_BOUNDS = -7
 LBM_ERR_PIVOT = -6
 LBM_ERR_UNSUPPORTED = -8
+LBM_ERR_BARRIER = -9
 LBM_BC_PERIODIC = 0
 LBM_BC_EQ_ZEROGRAD_U0LEFT = 1
 LBM_FP64 = 0
@@ -106,7 +107,7 @@ EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
             "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe",
             "lbm_adjoint_workspace_bytes", "lbm_adjoint_step", "lbm_heat_release_gradient",
-            "lbm_flame_speeds", "lbm_isoline_means"]
+            "lbm_flame_speeds", "lbm_isoline_means", "lbm_step_persistent", "lbm_autotune_persistent"]
 
 
 def library_path() -> str:
@@ -274,6 +275,20 @@ def lbm_heat_release_gradient(ctx, nsteps: int, checkpoint_every: int, J: np.nda
                                           dlogA.ctypes.data_as(_dp) if dlogA is not None else None,
                                           C.c_void_p(dT0_ptr) if dT0_ptr else None, C.c_void_p(ws_ptr),
                                           int(ws_bytes))
+
+
+_lib.lbm_step_persistent.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_uint]
+_lib.lbm_autotune_persistent.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
+
+
+def lbm_step_persistent(ctx, n: int, tile_mult: int = 1, spin_cap: int = 0) -> int:
+    return _lib.lbm_step_persistent(ctx, int(n), int(tile_mult), C.c_uint(spin_cap))
+
+
+def lbm_autotune_persistent(ctx, steps: int):
+    out = C.c_int(0)
+    st = _lib.lbm_autotune_persistent(ctx, int(steps), C.byref(out))
+    return st, int(out.value)
 
 
 _lib.lbm_flame_speeds.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
@@ -469,6 +484,21 @@ class Solver:
     def step_graph(self, n: int = 1):
         """n steps through the captured two-step CUDA graph (no wait)."""
         _check(lbm_step_graph(self.ctx, n), "lbm_step_graph")
+
+    @_on_device
+    def step_persistent(self, n: int = 1, tile_mult: int = 1, spin_cap: int = 0, check: bool = True) -> int:
+        """n steps in one persistent cooperative launch (see lbm_step_persistent)."""
+        st = lbm_step_persistent(self.ctx, n, tile_mult, spin_cap)
+        if check:
+            _check(st, "lbm_step_persistent")
+        return st
+
+    @_on_device
+    def autotune_persistent(self, steps: int = 4) -> int:
+        """The fastest tile_mult of lbm_step_persistent on the current state (unchanged)."""
+        st, t = lbm_autotune_persistent(self.ctx, steps)
+        _check(st, "lbm_autotune_persistent")
+        return t
 
     @_on_device
     def step_timed(self, n: int = 1):
