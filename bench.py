@@ -37,25 +37,24 @@ FALLBACK_HBM_GBS = 6800.0
 SM_COUNT, FP64_FMA_PER_SM_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_TFLOPS_DERIVED = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
-# Per lattice node and launch, counted by ncu on the 128^3 instance of this
-# workload for the kernels as they stand (profiles/ has the captures):
-#   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions;
-#   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum.
+# Per lattice node and launch, counted by ncu for the kernels as they
+# stand (profiles/ has the captures and their commands):
+#   FP64 flops = 2 x DFMA + DADD + DMUL thread instructions (64^3 instance:
+#   instruction counts per node do not depend on the lattice size);
+#   DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum on the 256^3
+#   lattice itself (a smaller one keeps part of its state in L2).
 # The production rates are formed inside k_step (no k_chem launch), so
-# their flops count there (double unit: the sum of the two kernels' counts
-# taken before they were fused; the instructions are the same).  k_pre was
-# counted before its finiteness and sign checks moved to the integer pipe,
-# which removed compares, not flops.
+# their flops count there.
 FP64_FLOPS_PER_NODE = {
-    "mixed": {"k_pre": 2054.4, "k_step_g": 165.0, "k_step": 1189.0},
-    "mixed_fast": {"k_pre": 723.0, "k_step_g": 165.0, "k_step": 663.0},
-    "fp64": {"k_pre": 2859.4, "k_step_g": 737.0, "k_step": 13706.0},
+    "mixed": {"k_pre": 1896.4, "k_step_g": 165.0, "k_step": 1189.0},
+    "mixed_fast": {"k_pre": 647.2, "k_step_g": 165.0, "k_step": 663.0},
+    "fp64": {"k_pre": 2584.4, "k_step_g": 737.0, "k_step": 13670.0},
 }
 # lbm_heat_release (k_hrr: moments, temperature, hdot^c and its derivatives
 # per node), counted the same way; None until counted.
-HRR_FLOPS_PER_NODE = {"mixed": 3105.9, "mixed_fast": None, "fp64": None}
+HRR_FLOPS_PER_NODE = {"mixed": 3123.0, "mixed_fast": None, "fp64": None}
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2105.5, "k_step_g": 600.3, "k_step": 2401.0},
+    "mixed": {"k_pre": 2085.9, "k_step_g": 617.4, "k_step": 2466.7},
     "mixed_fast": {"k_pre": 2275.2, "k_step_g": 600.5, "k_step": 2398.0},
     "fp64": {"k_pre": 3415.9, "k_step_g": 699.7, "k_step": 4458.0},
 }

@@ -490,6 +490,15 @@ int lbm_step_fixed_scratch(const lbm_lattice *lat, const lbm_species *sp, const 
  * the stream; LBM_ERR_ARG for NULL pointers or n < 0. */
 int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream);
 
+/* Diagnostic (the paper has no counterpart): the kernels convert between
+ * float and double with integer operations (the hardware conversion issues
+ * on the FP64 pipe).  Writes those conversions of f [n] to fd and of d [n]
+ * to df, and the hardware conversions (round to nearest even) to fd_ref
+ * and df_ref.  All pointers device; waits for the stream; LBM_ERR_ARG for
+ * NULL pointers or n < 0. */
+int lbm_convert_check(const float *f, double *fd, double *fd_ref, const double *d, float *df, float *df_ref,
+                      int n, void *cuda_stream);
+
 /* Flame diagnostics of the circular expanding flame (paper Sec. 5b) at the
  * current state (the state the next collision sees): per node the local
  * displacement speed of Eq. (sd),

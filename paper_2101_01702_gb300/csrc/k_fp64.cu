@@ -11,7 +11,29 @@ __global__ void k_exp_check(const double *x, double *y, double *y_ref, int n)
     y[i] = exp_table(x[i]);
     y_ref[i] = exp(x[i]);
 }
+
+__global__ void k_convert_check(const float *f, double *fd, double *fd_ref, const double *d, float *df, float *df_ref,
+                                int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fd[i] = f2d(f[i]);
+    fd_ref[i] = (double)f[i];
+    df[i] = d2f(d[i]);
+    df_ref[i] = __double2float_rn(d[i]);
+}
 }  // namespace
+
+extern "C" int lbm_convert_check(const float *f, double *fd, double *fd_ref, const double *d, float *df,
+                                 float *df_ref, int n, void *cuda_stream)
+{
+    if (!f || !fd || !fd_ref || !d || !df || !df_ref || n < 0) return LBM_ERR_ARG;
+    if (n == 0) return LBM_OK;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    k_convert_check<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, fd, fd_ref, d, df, df_ref, n);
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
 
 extern "C" int lbm_exp_check(const double *x, double *y, double *y_ref, int n, void *cuda_stream)
 {

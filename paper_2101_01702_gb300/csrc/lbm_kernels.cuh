@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -175,6 +176,48 @@ __device__ __forceinline__ bool nonzero_bits(double x)
     return ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) != 0;
 }
 __device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x) & 0x7fffffff) != 0; }
+
+// Conversions between float and double on the integer pipe.  A hardware
+// conversion between the two issues on the FP64 pipe, which bounds the
+// moment pass; these give the same IEEE 754 result (binary32 <-> binary64,
+// double -> float rounded to nearest, ties to even) with integer
+// operations for zeros and normal results.  A warp with a lane outside
+// that range (subnormals, overflow, Inf, NaN: rare here) takes the
+// hardware conversion for all its lanes; the test is a warp vote, so the
+// branch is uniform and the common path issues no FP64 instruction.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f), mag = b & 0x7fffffffu;
+    const bool rare = (mag >> 23) - 1u >= 254u && mag != 0u;            // subnormal, Inf, NaN
+    if (__builtin_expect(__any_sync(__activemask(), rare), 0)) return (double)f;
+    // exponent rebiased by 1023 - 127 = 896; the low 3 mantissa bits move to the low word
+    const unsigned hi = (b & 0x80000000u) | (mag ? (mag >> 3) + (896u << 20) : 0u);
+    return __hiloint2double((int)hi, (int)(mag << 29));
+}
+
+__device__ __forceinline__ float d2f(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned hm = hi & 0x7fffffffu;
+    const bool zero = (hm | lo) == 0u;
+    // normal float results: biased double exponent in [897, 1150]
+    const bool rare = (hm >> 20) - 897u > 253u && !zero;
+    if (__builtin_expect(__any_sync(__activemask(), rare), 0)) return __double2float_rn(d);
+    const unsigned m = ((hm - (896u << 20)) << 3) | (lo >> 29);     // float exponent and mantissa, truncated
+    const unsigned rem = lo & 0x1fffffffu;                          // the 29 bits dropped
+    const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & m);
+    return __uint_as_float((hi & 0x80000000u) | (zero ? 0u : m + up));   // a carry rounds into the exponent
+}
+
+// x converted to To (a plain copy when the types agree).
+template <class To, class From>
+__device__ __forceinline__ To cvt(From x)
+{
+    if constexpr (std::is_same<To, From>::value) return x;
+    else if constexpr (std::is_same<To, double>::value && std::is_same<From, float>::value) return f2d(x);
+    else if constexpr (std::is_same<To, float>::value && std::is_same<From, double>::value) return d2f(x);
+    else return (To)x;
+}
 
 // Checked builds: records a failed index check; always true otherwise.
 __device__ __forceinline__ bool index_ok(bool ok, unsigned *status)
@@ -668,6 +711,7 @@ __device__ __forceinline__ void row_moments(LD &&ld, V &s0, V &sx, V &sy, V &sz,
 // f gives rho, j and (WITH_P) the pressure tensor; g gives rho E and q.
 struct Sums {
     double rho, j[3], P[6], rhoE, q[3];   // P: xx, yy, zz, xy, xz, yz
+    Real jr[3];                           // j as summed, in the storage type
 };
 
 // In the mixed units the moving populations are summed as the stored float
@@ -699,7 +743,7 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
             return pull_sf(mc, v, a, s, I, p);
 #endif
         }, a0, ax, ay, az, nullptr);
-        rho_a[s] = (double)a0;
+        rho_a[s] = cvt<double>(a0);
 #if LBMK_MIXED
         rho_a[s] += mc.ref0[s] + v.rest()[(size_t)s * a.N + n];
 #endif
@@ -719,12 +763,13 @@ __device__ __forceinline__ void pull_moments(const MechConst &mc, const StepArgs
         return pull_sf(mc, v, a, M - 1, I, p);
 #endif
     }, a0, ax, ay, az, P6);
-    sm.rho = (double)a0;
+    sm.rho = cvt<double>(a0);
     sm.rhoE = g0;
-    sm.j[0] = ax; sm.j[1] = ay; sm.j[2] = az;
+    sm.jr[0] = ax; sm.jr[1] = ay; sm.jr[2] = az;
+    sm.j[0] = cvt<double>(ax); sm.j[1] = cvt<double>(ay); sm.j[2] = cvt<double>(az);
     sm.q[0] = qx; sm.q[1] = qy; sm.q[2] = qz;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) sm.P[k] = WITH_P ? (double)P6[k] : 0.0;
+    for (int k = 0; k < 6; ++k) sm.P[k] = WITH_P ? cvt<double>(P6[k]) : 0.0;
 #if LBMK_MIXED
     sm.rho += mc.ref0[M - 1] + v.rest()[(size_t)(M - 1) * a.N + n];
     if constexpr (WITH_P)
@@ -1090,7 +1135,7 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
     rho_a[M - 1] = rho - rest;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        Real js = (Real)sm.j[d];
+        Real js = sm.jr[d];
 #pragma unroll
         for (int s = 0; s < M - 1; ++s) js -= ja[s][d];
         ja[M - 1][d] = js;
@@ -1129,8 +1174,8 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
     if (mc.transport) {
         mixture_transport<M>(mc, Y, inv_m, T, P, Cv + Rm, nup, nup1, dfac);
     } else {
-        nup = (Real)nu_prime(mc, Rm, T);
-        nup1 = nup / (Real)mc.Pr;
+        nup = cvt<Real>(nu_prime(mc, Rm, T));
+        nup1 = nup / cvt<Real>(mc.Pr);
     }
     const Real omega = (Real)1 / ((Real)0.5 + nup);
     const Real omega1 = (Real)1 / ((Real)0.5 + nup1);
@@ -1149,10 +1194,10 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
     // (the results are stored as floats there, and the solve below is well
     // conditioned: B is diagonally dominant after the symmetric scaling by Y).
     const double kappa = mc.transport ? mc.r_lat * T / (inv_m * dfac) : mc.r_lat * T / inv_m;
-    const SReal kap = (SReal)kappa, irr = (SReal)ir;
-    SReal Yr[M], ur[3] = {(SReal)u[0], (SReal)u[1], (SReal)u[2]};
+    const SReal kap = cvt<SReal>(kappa), irr = cvt<SReal>(ir);
+    SReal Yr[M], ur[3] = {cvt<SReal>(u[0]), cvt<SReal>(u[1]), cvt<SReal>(u[2])};
 #pragma unroll
-    for (int s = 0; s < M; ++s) Yr[s] = (SReal)Y[s];
+    for (int s = 0; s < M; ++s) Yr[s] = cvt<SReal>(Y[s]);
     SReal ita[M];
 #pragma unroll
     for (int s = 0; s < M; ++s) {
@@ -1206,7 +1251,7 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
         for (int i = 0; i < M; ++i)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                SReal sacc = fma((SReal)ja[i][d], irr, -Yr[i] * ur[d]);
+                SReal sacc = fma(cvt<SReal>(ja[i][d]), irr, -Yr[i] * ur[d]);
 #pragma unroll
                 for (int j = 0; j < i; ++j) sacc = fma(-Ln[i][j], du[j][d], sacc);
                 du[i][d] = sacc;
@@ -1246,19 +1291,19 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
         Real HY[M];
 #pragma unroll
         for (int s = 0; s < M; ++s) {
-            HaR[s] = (Real)Ha[s];
-            YR[s] = (Real)Yr[s];
+            HaR[s] = cvt<Real>(Ha[s]);
+            YR[s] = cvt<Real>(Yr[s]);
             HY[s] = HaR[s] * YR[s];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) duR[s][d] = (Real)du[s][d];
+            for (int d = 0; d < 3; ++d) duR[s][d] = cvt<Real>(du[s][d]);
         }
-        const Real orho = omega1 * (Real)rho;
+        const Real orho = omega1 * cvt<Real>(rho);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             Real hyd = 0;
 #pragma unroll
             for (int s = 0; s < M; ++s) hyd = fma(HY[s], duR[s][d], hyd);
-            dq[d] = (omega - omega1) * (Real)(sm.q[d] - uP[d] - qeq[d]) + orho * hyd;
+            dq[d] = (omega - omega1) * cvt<Real>(sm.q[d] - uP[d] - qeq[d]) + orho * hyd;
         }
     }
 
@@ -1287,10 +1332,10 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
     Real *R = rec(a);
     R[(size_t)rr.nup * N + n] = nup;
     // Phi (Eq. (Xalpha)), stored in the storage type and formed in it
-    const Real rhoR = (Real)rho, rtR = (Real)(Rm * T), ph = (Real)1 - (Real)3 * rtR;
+    const Real rhoR = cvt<Real>(rho), rtR = cvt<Real>(Rm * T), ph = (Real)1 - (Real)3 * rtR;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const Real ud = (Real)ur[d];
+        const Real ud = cvt<Real>(ur[d]);
         R[(size_t)(rr.phi + d) * N + n] = rhoR * ud * (ph - ud * ud);
         R[(size_t)(rr.u + d) * N + n] = ud;
         R[(size_t)(rr.dq + d) * N + n] = dq[d];
@@ -1302,16 +1347,16 @@ __device__ __forceinline__ void pre_node(const StepArgs &a, const Node &nd)
         for (int d = 0; d < 3; ++d) R[(size_t)(rr.du + 3 * s + d) * N + n] = duR[s][d];
         // beta_a = 1/(2 tau_a + 1), Eq. (fStar): a parameter of the species
         // collision, formed in the storage type it is used in
-        const Real it = (Real)ita[s];
+        const Real it = cvt<Real>(ita[s]);
         R[(size_t)(rr.beta + s) * N + n] = it / ((Real)2 + it);
         R[(size_t)(rr.h + s) * N + n] = HaR[s];
     }
     R[(size_t)rr.rho * N + n] = rhoR;
-    R[(size_t)rr.kappa * N + n] = (Real)kap;
+    R[(size_t)rr.kappa * N + n] = cvt<Real>(kap);
     R[(size_t)rr.rt * N + n] = rtR;
     R[(size_t)rr.om * N + n] = omega;
     R[(size_t)rr.om1 * N + n] = omega1;
-    R[(size_t)rr.p * N + n] = (Real)P;
+    R[(size_t)rr.p * N + n] = cvt<Real>(P);
 }
 
 template <int M>

@@ -103,7 +103,7 @@ _lib.lbm_strerror.restype = C.c_char_p
 EXPORTED = ["lbm_buffer_sizes", "lbm_create", "lbm_init", "lbm_step", "lbm_step_async", "lbm_step_graph",
             "lbm_step_timed", "lbm_sync",
             "lbm_moments", "lbm_moments_count", "lbm_get_populations", "lbm_state_buffer", "lbm_destroy",
-            "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_get_references",
+            "lbm_strerror", "lbm_step_fixed_scratch", "lbm_exp_check", "lbm_convert_check", "lbm_get_references",
             "lbm_set_references", "lbm_autotune", "lbm_set_blocks", "lbm_heat_release",
             "lbm_chemistry_at", "lbm_temperature_at", "lbm_heat_release_adjoint", "lbm_fp64_probe",
             "lbm_adjoint_workspace_bytes", "lbm_adjoint_step", "lbm_heat_release_gradient",
@@ -239,6 +239,16 @@ def lbm_destroy(ctx) -> int:
 
 _lib.lbm_exp_check.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.lbm_exp_check.restype = C.c_int
+
+
+_lib.lbm_convert_check.argtypes = [C.c_void_p] * 6 + [C.c_int, C.c_void_p]
+_lib.lbm_convert_check.restype = C.c_int
+
+
+def lbm_convert_check(f_ptr: int, fd_ptr: int, fd_ref_ptr: int, d_ptr: int, df_ptr: int, df_ref_ptr: int, n: int,
+                      stream: int) -> int:
+    return _lib.lbm_convert_check(*(C.c_void_p(p) for p in (f_ptr, fd_ptr, fd_ref_ptr, d_ptr, df_ptr, df_ref_ptr)),
+                                  int(n), C.c_void_p(stream))
 
 
 def lbm_exp_check(x_ptr: int, y_ptr: int, y_ref_ptr: int, n: int, stream: int) -> int:
