@@ -54,7 +54,7 @@ FP64_FLOPS_PER_NODE = {
 # per node), counted the same way; None until counted.
 HRR_FLOPS_PER_NODE = {"mixed": 3123.0, "mixed_fast": None, "fp64": None}
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2085.9, "k_step_g": 617.4, "k_step": 2466.7},
+    "mixed": {"k_pre": 2163.7, "k_step_g": 617.3, "k_step": 2468.5},
     "mixed_fast": {"k_pre": 2275.2, "k_step_g": 600.5, "k_step": 2398.0},
     "fp64": {"k_pre": 3415.9, "k_step_g": 699.7, "k_step": 4458.0},
 }
@@ -770,7 +770,9 @@ def run_flames(args):
 def run_accuracy(args):
     """Field error of the mixed modes against the double GPU step on the
     whole benchmark lattice after K steps: max |F - F_fp64| / max |F_fp64|
-    for T and for each Y_a (the 1e-4 bar of the mixed-precision design)."""
+    for T and for each Y_a (the 1e-4 bar of the mixed-precision design).
+    The three runs advance side by side, so --accuracy-every E also records
+    the errors every E steps (the growth of the error in time)."""
     import torch
     import workload as w
     from paper_2101_01702_gb300 import build
@@ -780,31 +782,43 @@ def run_accuracy(args):
     n = args.size
     prob = w.sphere3d_problem(n=n, radius=20.0 * n / 256.0)
     K = args.accuracy_steps
+    every = args.accuracy_every if args.accuracy_every > 0 else K
     mask = lbm.LBM_F_T | lbm.LBM_F_Y
-
-    def run(precision):
-        s = lbm.Solver.from_problem(prob, precision=precision)
-        t0 = time.perf_counter()
-        s.step(K)
-        dt = time.perf_counter() - t0
-        m = s.moments(mask, device=True)
-        s.close()
-        del s
-        torch.cuda.empty_cache()
-        return m, dt
-
-    ref, t_ref = run(lbm.LBM_FP64)
+    modes = (("fp64", lbm.LBM_FP64), ("mixed", lbm.LBM_MIXED), ("mixed_fast", lbm.LBM_MIXED_FAST))
+    solvers = {name: lbm.Solver.from_problem(prob, precision=p) for name, p in modes}
+    seconds = {name: 0.0 for name, _ in modes}
+    history = []
+    done = 0
     out = {"metric": f"relative field error after {K} steps against the double GPU step",
-           "config": {"workload": f"sphere3d_{n}^3_M9", "nodes": prob.lattice.n_nodes, "steps": K},
-           "fp64_seconds": t_ref}
-    for name, precision in (("mixed", lbm.LBM_MIXED), ("mixed_fast", lbm.LBM_MIXED_FAST)):
-        m, dt = run(precision)
-        errT = float(((m["T"] - ref["T"]).abs().max() / ref["T"].abs().max()).item())
-        errY = [float(((m["Y"][a] - ref["Y"][a]).abs().max() / ref["Y"][a].abs().max()).item())
-                for a in range(prob.species.M)]
-        out[name] = {"T": errT, "Y": errY, "max": max([errT] + errY), "seconds": dt}
-        del m
+           "config": {"workload": f"sphere3d_{n}^3_M9", "nodes": prob.lattice.n_nodes, "steps": K}}
+    while done < K:
+        k = min(every, K - done)
+        for name, _ in modes:
+            t0 = time.perf_counter()
+            solvers[name].step(k)
+            seconds[name] += time.perf_counter() - t0
+        done += k
+        ref = solvers["fp64"].moments(mask, device=True)
+        rec = {"step": done}
+        for name in ("mixed", "mixed_fast"):
+            m = solvers[name].moments(mask, device=True)
+            errT = float(((m["T"] - ref["T"]).abs().max() / ref["T"].abs().max()).item())
+            errY = [float(((m["Y"][a] - ref["Y"][a]).abs().max() / ref["Y"][a].abs().max()).item())
+                    for a in range(prob.species.M)]
+            rec[name] = {"T": errT, "Y": errY, "max": max([errT] + errY)}
+            del m
+        del ref
         torch.cuda.empty_cache()
+        history.append(rec)
+    for name in ("mixed", "mixed_fast"):
+        out[name] = dict(history[-1][name], seconds=seconds[name])
+    out["fp64_seconds"] = seconds["fp64"]
+    if len(history) > 1:
+        out["history"] = [{"step": h["step"], "mixed": h["mixed"]["max"], "mixed_fast": h["mixed_fast"]["max"],
+                           "mixed_argmax": max(range(len(h["mixed"]["Y"])), key=lambda a: h["mixed"]["Y"][a])}
+                          for h in history]
+    for s in solvers.values():
+        s.close()
     print(json.dumps(out), flush=True)
 
 
@@ -830,6 +844,8 @@ def main():
     ap.add_argument("--cpu-legs", action="store_true",
                     help="instead of timing the GPU: the oracle's timed legs (64x4x4 200 steps, 32^3 1000 steps, "
                          "256^3 10 steps)")
+    ap.add_argument("--accuracy-every", type=int, default=0,
+                    help="with --accuracy-steps: also record the errors every this many steps")
     ap.add_argument("--accuracy-steps", type=int, default=0,
                     help="instead of timing: field error of the mixed modes against double after this many steps")
     args = ap.parse_args()

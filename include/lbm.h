@@ -228,10 +228,10 @@ int lbm_step_graph(lbm_ctx *ctx, int n);
  * in each phase of a step (ghost planes, the per-node record, G, the
  * energy collision, the species collision) their warps take chunks of
  * tile_mult x 32 consecutive nodes from a queue, and all meet at a grid
- * barrier before the next phase.  Results are bit for bit those of
- * lbm_step in the mixed units; in the double unit they agree to rounding
+ * barrier before the next phase.  Results agree with lbm_step to rounding
  * (the compiler may fuse a multiply and an add in this kernel where it does
- * not in the separate ones: about one unit in the last place per step).  Each barrier polls a device word at most spin_cap times
+ * not in the separate ones: about one unit in the last place per step).
+ * Each barrier polls a device word at most spin_cap times
  * (0: 1 << 24, about two seconds); a block that runs out records
  * LBM_ERR_BARRIER and returns, the others then run out at the next barrier,
  * so the launch always ends -- the state is then partly stepped and must be

@@ -376,17 +376,13 @@ __device__ __forceinline__ double pull_g(const PopView &v, const StepArgs &a, in
     return sr.ghost ? load_ghost(a, sr.side, a.M, i, sr.idx) : load_g(v, i, sr.idx);
 }
 
-// Writers of the post-collision state at node n.  store_mov writes a
-// moving population of a species/mixture set in the storage precision
-// (no conversion through double); store_sf also takes the rest direction.
-__device__ __forceinline__ void store_mov(const MechConst &mc, void *buf, const StepArgs &a, int s, int i, size_t n,
-                                          Real v)
+// Writers of the post-collision state at node n.  store_raw writes the
+// stored value of a moving population of a species/mixture set: in the
+// mixed units its deviation from the rest state RAWREF(s, i), in double
+// the population; store_sf takes an absolute double value, any direction.
+__device__ __forceinline__ void store_raw(void *buf, const StepArgs &a, int s, int i, size_t n, Real v)
 {
-#if LBMK_MIXED
-    static_cast<float *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v - mc.ref[s][i];
-#else
-    static_cast<double *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v;
-#endif
+    static_cast<Real *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v;
 }
 
 __device__ __forceinline__ void store_sf(const MechConst &mc, void *buf, const StepArgs &a, int s, int i, size_t n,
@@ -470,7 +466,10 @@ __device__ __forceinline__ double dpoly5(const double u[6], double T)
     return fma(fma(fma(fma(5.0 * u[5], T, 4.0 * u[4]), T, 3.0 * u[3]), T, 2.0 * u[2]), T, u[1]);
 }
 
-// Newton iteration on U(T) = e from T; stops when |dT| <= 1e-13 T.
+// Newton iteration on U(T) = e from T.  It stops once a correction is at
+// most 1e-7 T: Newton's error after that step is about (C_v'/2C_v) dT^2,
+// below 1e-13 T for these polynomials (C_v'/C_v is of order 1/T), so the
+// further iteration a 1e-13 test would take changes T by less than that.
 __device__ __forceinline__ double solve_T(const double u[6], double e, double T, unsigned *status)
 {
     const double d5 = 5.0 * u[5], d4 = 4.0 * u[4], d3 = 3.0 * u[3], d2 = 2.0 * u[2];   // C_v's coefficients
@@ -480,7 +479,7 @@ __device__ __forceinline__ double solve_T(const double u[6], double e, double T,
         const double dT = F / Fp;
         T -= dT;
         if (!finite_bits(T)) { flag(status, LBMK_BIT_NONFINITE); return T; }
-        if (fabs(dT) <= 1e-13 * fabs(T)) return T;
+        if (fabs(dT) <= 1e-7 * fabs(T)) return T;
     }
     flag(status, LBMK_BIT_NEWTON);
     return T;
@@ -1707,19 +1706,23 @@ __device__ __forceinline__ void step_node(const StepArgs &a, const Node &nd)
             for (int b = 0; b < M; ++b)
                 if (b != s) F += INVWWD(s, b) * Dl[b];
             F *= kappa * Yl[s];
-            const Real feq = rho * Yl[s] * eqp[s];
-            const Real f = fc[s] + RAWREF(s, i);
-            const Real val = f + (Real)2 * bt[s] * (feq - f) + (bt[s] - (Real)1) * F + wd[s] * eqp[s];
-            store_mov(mc, a.dst, a, s, i, n, val);
+            // in deviations from the rest state (the stored values; the
+            // moments of k_pre are summed from them too): f - r relaxes to
+            // feq - r, and the result is stored as it is
+            // (explicit fma: the same roundings in every kernel this is inlined into)
+            const Real feq = fma(rho * Yl[s], eqp[s], -RAWREF(s, i));
+            const Real fd = fc[s];
+            const Real val = fma(wd[s], eqp[s], fma(bt[s] - (Real)1, F, fma((Real)2 * bt[s], feq - fd, fd)));
+            store_raw(a.dst, a, s, i, n, val);
             check += val;
         }
         // mixture f: Eq. (f) with the isotropy correction A_i . X (Eq. (Ai))
         {
-            const Real feq = psi_c(cx, u[0], u2[0] + RT) * fe_yz;
+            const Real feq = fma(psi_c(cx, u[0], u2[0] + RT), fe_yz, -RAWREF(M - 1, i));
             const Real AX = cx == 0 ? AXyz : (j == 4 ? (Real)0.5 * (Real)cx * X[0] : (Real)0);
-            const Real f = fc[M - 1] + RAWREF(M - 1, i);
-            const Real val = f + om * (feq - f) + AX;
-            store_mov(mc, a.dst, a, M - 1, i, n, val);
+            const Real fd = fc[M - 1];
+            const Real val = fma(om, feq - fd, fd) + AX;
+            store_raw(a.dst, a, M - 1, i, n, val);
             check += val;
         }
     }

@@ -5,11 +5,11 @@ a poll limit.
 * On a ragged batch of quasi-1D flames (per-flame ghost faces, lengths not
   multiples of the 128-thread block) and on a periodic lattice, the
   populations and the temperature row equal those of lbm_step, for several
-  tile lengths and odd step counts (the buffer parity): bit for bit in the
-  mixed units; in the double unit to 1e-12 of each set's largest value,
-  since the compiler may fuse a multiply and an add in the combined kernel
-  where it does not in the species collision's own kernel (one rounding of
-  difference, seen as 1e-16 after one step).
+  tile lengths and odd step counts (the buffer parity), to rounding: the
+  compiler may fuse a multiply and an add inside the combined kernel where
+  it does not in a phase's own kernel (one rounding of difference per
+  step).  Bounds: 1e-12 of each set's largest value in double, 1e-6 in the
+  float units; the temperature row 1e-13 and 1e-7 of its maximum.
 * A poll limit of one makes a barrier give up: the call returns
   LBM_ERR_BARRIER, returns at all (no hang), and the context steps
   correctly again once re-initialised.
@@ -48,13 +48,10 @@ def _state(s, n_nodes):
 
 
 def _same(mode, pa, pb, ta, tb):
-    if mode != "fp64":
-        assert np.array_equal(pa, pb)
-        assert np.array_equal(ta, tb)
-        return
+    tp, tt = (1e-12, 1e-13) if mode == "fp64" else (1e-6, 1e-7)
     scale = np.abs(pa).max(axis=(1, 2), keepdims=True)
-    assert (np.abs(pa - pb) <= 1e-12 * scale).all(), float((np.abs(pa - pb) / scale).max())
-    assert np.abs(ta - tb).max() <= 1e-13 * np.abs(ta).max()
+    assert (np.abs(pa - pb) <= tp * scale).all(), float((np.abs(pa - pb) / scale).max())
+    assert np.abs(ta - tb).max() <= tt * np.abs(ta).max(), float(np.abs(ta - tb).max())
 
 
 def _pair(L, prob, mode):
@@ -110,8 +107,8 @@ def test_poll_limit_runs_out_and_the_context_recovers(lbm):
     assert s.sync() == lbm.LBM_OK            # the status word was cleared
     s.init(prob.init.X, prob.init.T, prob.init.u, prob.init.P)
     s.step_persistent(4)
-    got = _state(s, n)
-    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    pb, tb = _state(s, n)
+    _same("mixed", want[0], pb, want[1], tb)
     s.close()
 
 
@@ -125,7 +122,9 @@ def test_autotune_keeps_the_state(lbm):
     assert t in (1, 2, 4, 8)
     a.step(4)
     b.step_persistent(4, tile_mult=t)
-    assert np.array_equal(_state(a, n)[0], _state(b, n)[0])
+    pa, ta = _state(a, n)
+    pb, tb = _state(b, n)
+    _same("mixed", pa, pb, ta, tb)
     a.close()
     b.close()
 
