@@ -46,15 +46,15 @@ FP64_PEAK_TFLOPS_DERIVED = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6
 # The production rates are formed inside k_step (no k_chem launch), so
 # their flops count there.
 FP64_FLOPS_PER_NODE = {
-    "mixed": {"k_pre": 1896.4, "k_step_g": 165.0, "k_step": 1189.0},
-    "mixed_fast": {"k_pre": 647.2, "k_step_g": 165.0, "k_step": 663.0},
-    "fp64": {"k_pre": 2584.4, "k_step_g": 737.0, "k_step": 13670.0},
+    "mixed": {"k_pre": 1873.6, "k_step_g": 165.0, "k_step": 1189.0},
+    "mixed_fast": {"k_pre": 621.5, "k_step_g": 165.0, "k_step": 663.0},
+    "fp64": {"k_pre": 2561.6, "k_step_g": 737.0, "k_step": 13688.0},
 }
 # lbm_heat_release (k_hrr: moments, temperature, hdot^c and its derivatives
 # per node), counted the same way; None until counted.
 HRR_FLOPS_PER_NODE = {"mixed": 3123.0, "mixed_fast": None, "fp64": None}
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2163.7, "k_step_g": 617.3, "k_step": 2468.5},
+    "mixed": {"k_pre": 2165.6, "k_step_g": 617.3, "k_step": 2437.5},
     "mixed_fast": {"k_pre": 2275.2, "k_step_g": 600.5, "k_step": 2398.0},
     "fp64": {"k_pre": 3415.9, "k_step_g": 699.7, "k_step": 4458.0},
 }
