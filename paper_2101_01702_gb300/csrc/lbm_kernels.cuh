@@ -393,7 +393,7 @@ __device__ __forceinline__ void store_sf(const MechConst &mc, void *buf, const S
     if (i == REST) {
         reinterpret_cast<double *>(static_cast<char *>(buf) + pop_float_bytes(a.M, N))[(size_t)s * N + n] = v;
     } else {
-        static_cast<float *>(buf)[((size_t)s * LBMK_Q + i) * N + n] = (float)v - mc.ref[s][i];
+        static_cast<float *>(buf)[((size_t)s * LBMK_Q + i) * N + n] = cvt<float>(v) - mc.ref[s][i];
     }
 #else
     static_cast<double *>(buf)[((size_t)s * LBMK_Q + i) * a.N + n] = v;
@@ -1039,7 +1039,7 @@ __device__ __forceinline__ void molar_production(const MechConst &mc, double T, 
                 q *= Pr / (1.0 + Pr);
             }
         }
-        const WReal qr = (WReal)q;
+        const WReal qr = cvt<WReal>(q);
         for (int j = 0; j < nr; ++j) sh_w[mc.reac[k][j] * stride + t] -= qr;
         for (int j = 0; j < np; ++j) sh_w[mc.prod[k][j] * stride + t] += qr;
     }
@@ -1584,7 +1584,7 @@ __device__ __forceinline__ void step_node(const StepArgs &a, const Node &nd)
     const Real rho = ld(rr.rho), om = ld(rr.om);
     const Real kappa = ld(rr.kappa), RT = ld(rr.rt);
     const Real u[3] = {ld(rr.u), ld(rr.u + 1), ld(rr.u + 2)};
-    const Real T = (Real)ldd(DR_T);
+    const Real T = cvt<Real>(ldd(DR_T));
 
     // per-species data: mass fraction, quasi-equilibrium velocity u + du_b,
     // beta_b and rho_dot_b (densities, zeta and the products are formed per
@@ -1605,10 +1605,10 @@ __device__ __forceinline__ void step_node(const StepArgs &a, const Node &nd)
         // the production rates of this node, as k_chem forms them
         double conc[M];
 #pragma unroll
-        for (int s = 0; s < M; ++s) conc[s] = (double)rho * (double)Yl[s] * mc.invW[s];
+        for (int s = 0; s < M; ++s) conc[s] = cvt<double>(rho) * cvt<double>(Yl[s]) * mc.invW[s];
         molar_production<M>(mc, ldd(DR_T), conc, sh_act, sh_g, sh_w, threadIdx.x, LBMK_BLOCK);
 #pragma unroll
-        for (int s = 0; s < M; ++s) wd[s] = (Real)(mc.W[s] * sh_w[s * LBMK_BLOCK + threadIdx.x]);
+        for (int s = 0; s < M; ++s) wd[s] = cvt<Real>(mc.W[s] * sh_w[s * LBMK_BLOCK + threadIdx.x]);
     }
 #endif
     const Real u2[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
@@ -1750,15 +1750,15 @@ __device__ __forceinline__ void step_node(const StepArgs &a, const Node &nd)
                 if (b != s) F += INVWWD(s, b) * Dl[b];
             F *= kappa * Yl[s];
             const double f0 = rs[(size_t)s * N + n];
-            const Real diff = (Real)(ldd(DR_FEQ0 + s) - f0);
-            const double val = f0 + (double)((Real)2 * bt[s] * diff + (bt[s] - (Real)1) * F + wd[s] * eqp[s]);
+            const Real diff = cvt<Real>(ldd(DR_FEQ0 + s) - f0);
+            const double val = f0 + cvt<double>((Real)2 * bt[s] * diff + (bt[s] - (Real)1) * F + wd[s] * eqp[s]);
             store_sf(mc, a.dst, a, s, REST, n, val);
-            check += (Real)val;
+            check += cvt<Real>(val);
         }
         const double f0 = rs[(size_t)(M - 1) * N + n];
-        const double val = f0 + (double)(om * (Real)(ldd(DR_FEQ0 + M - 1) - f0));
+        const double val = f0 + cvt<double>(om * cvt<Real>(ldd(DR_FEQ0 + M - 1) - f0));
         store_sf(mc, a.dst, a, M - 1, REST, n, val);
-        check += (Real)val;
+        check += cvt<Real>(val);
     }
 #endif
     if (!isfinite(check)) flag(a.status, LBMK_BIT_NONFINITE);
