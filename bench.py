@@ -507,23 +507,28 @@ def run_ours(args):
         Th = torch.from_numpy(prob.init.T).pin_memory()
         mask = lbm.LBM_F_T | lbm.LBM_F_Y
         out = torch.empty(lbm.lbm_moments_count(s.ctx, mask), dtype=torch.float64).pin_memory()
-        runs = []
+        runs, parts = [], []
         for _ in range(3):                     # the whole job three times; the median is reported
             torch.cuda.synchronize()
             barrier()
+            # each call returns after its stream has drained, so the host
+            # clock between them splits the run into its three parts
             t0 = time.perf_counter()
             st = lbm.lbm_init(s.ctx, Xh.data_ptr(), Th.data_ptr(), None, prob.init.P)
+            t1 = time.perf_counter()
             st = st or lbm.lbm_step(s.ctx, args.steps)
+            t2 = time.perf_counter()
             st = st or lbm.lbm_moments(s.ctx, mask, out.data_ptr())
             torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
+            t3 = time.perf_counter()
             barrier()
             if st != lbm.LBM_OK:
                 raise lbm.LBMError(st, "e2e")
-            runs.append(N * args.steps * world / dt / 1e6)
+            runs.append(N * args.steps * world / (t3 - t0) / 1e6)
+            parts.append({"init_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3, "moments_out_ms": (t3 - t2) * 1e3})
         h2d = (M + 1) * N * 8
         d2h = out.numel() * 8
-        e2e = {"value": statistics.median(runs), "unit": "MLUPS", "runs": runs,
+        e2e = {"value": statistics.median(runs), "unit": "MLUPS", "runs": runs, "parts": parts,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "note": "lbm_init from pinned host fields + steps + lbm_moments(T, Y) to pinned host; "
                        "median of three whole runs"}
