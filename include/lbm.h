@@ -237,7 +237,9 @@ int lbm_step_graph(lbm_ctx *ctx, int n);
  * so the launch always ends -- the state is then partly stepped and must be
  * re-initialised or restored.  tile_mult >= 1.  Waits for the stream and
  * returns like lbm_sync (LBM_ERR_BARRIER after a timeout); LBM_ERR_ARG for
- * n < 0 or tile_mult < 1. */
+ * n < 0 or tile_mult < 1; LBM_ERR_UNSUPPORTED in a build whose production
+ * rates run in a kernel of their own (LBMK_FUSE_CHEM=0); LBM_ERR_CUDA when
+ * the device cannot hold the grid's blocks at once. */
 int lbm_step_persistent(lbm_ctx *ctx, int n, int tile_mult, unsigned spin_cap);
 
 /* Picks the tile length of lbm_step_persistent (tile_mult in 1, 2, 4, 8)
