@@ -54,7 +54,7 @@ FP64_FLOPS_PER_NODE = {
 # per node), counted the same way; None until counted.
 HRR_FLOPS_PER_NODE = {"mixed": 3123.0, "mixed_fast": None, "fp64": None}
 DRAM_BYTES_PER_NODE = {
-    "mixed": {"k_pre": 2165.6, "k_step_g": 617.3, "k_step": 2437.5},
+    "mixed": {"k_pre": 2165.2, "k_step_g": 617.3, "k_step": 2438.2},
     "mixed_fast": {"k_pre": 2275.2, "k_step_g": 600.5, "k_step": 2398.0},
     "fp64": {"k_pre": 3415.9, "k_step_g": 699.7, "k_step": 4458.0},
 }
